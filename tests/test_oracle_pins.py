@@ -1,0 +1,273 @@
+"""Pins for the CPU oracle: it must agree with mathematics, not only with itself.
+
+Every check compares the C oracle with something independent of it: Floyd-Warshall
+distances, exhaustive Def. 4 enumeration, closed forms, hand-worked examples, the
+textbook h = 1 triangle peel, and invariants the paper's definitions imply.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import pins
+from synth import barabasi_albert, erdos_renyi_gnm, rmat, small_corpus
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_examples.txt")
+
+
+def og(oracle_mod, n, edges):
+    eu = np.array([u for u, _ in edges], dtype=np.int32)
+    ev = np.array([v for _, v in edges], dtype=np.int32)
+    return oracle_mod.OracleGraph(n, eu, ev)
+
+
+def random_small(seed, n_max=8, m_max=12):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, n_max + 1))
+    allp = [(a, b) for a in range(n) for b in range(a + 1, n)]
+    m = int(rng.integers(1, min(m_max, len(allp)) + 1))
+    pick = rng.choice(len(allp), size=m, replace=False)
+    return n, sorted(allp[i] for i in pick)
+
+
+# ---- normalisation -------------------------------------------------------------------
+
+def test_normalise_matches_set_semantics(oracle_mod):
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        n = int(rng.integers(1, 30))
+        k = int(rng.integers(0, 80))
+        s = rng.integers(0, n, size=k).astype(np.int32)
+        d = rng.integers(0, n, size=k).astype(np.int32)
+        eu, ev = oracle_mod.normalise(n, s, d)
+        assert list(zip(eu.tolist(), ev.tolist())) == pins.canonical(n, s, d)
+
+
+def test_normalise_rejects_bad_ids(oracle_mod):
+    with pytest.raises(ValueError):
+        oracle_mod.normalise(3, [0, 1], [1, 3])
+    with pytest.raises(ValueError):
+        oracle_mod.normalise(3, [-1], [1])
+
+
+# ---- h-support against Floyd-Warshall --------------------------------------------------
+
+@pytest.mark.parametrize("h", [1, 2, 3, 4])
+def test_h_support_matches_floyd_warshall(oracle_mod, h):
+    for seed in range(40):
+        n, edges = random_small(1000 + seed, n_max=14, m_max=30)
+        g = og(oracle_mod, n, edges)
+        d = pins.apsp(n, edges)
+        np.testing.assert_array_equal(g.h_support(h), pins.sup_from_distances(d, edges, h))
+
+
+def test_h_support_on_subgraph_matches_floyd_warshall(oracle_mod):
+    rng = np.random.default_rng(7)
+    for seed in range(30):
+        n, edges = random_small(2000 + seed, n_max=12, m_max=25)
+        key = rng.integers(0, 4, size=len(edges)).astype(np.int32)
+        thr = int(rng.integers(0, 4))
+        mask = key >= thr
+        g = og(oracle_mod, n, edges)
+        for h in (1, 2, 3):
+            d = pins.apsp(n, edges, mask)
+            np.testing.assert_array_equal(
+                g.h_support(h, key, thr), pins.sup_from_distances(d, edges, h, mask))
+
+
+def test_h1_support_is_triangle_count(oracle_mod):
+    for seed in range(20):
+        n, edges = random_small(3000 + seed, n_max=20, m_max=60)
+        g = og(oracle_mod, n, edges)
+        adj = [set() for _ in range(n)]
+        for u, v in edges:
+            adj[u].add(v)
+            adj[v].add(u)
+        tri = [len(adj[u] & adj[v]) for u, v in edges]
+        np.testing.assert_array_equal(g.h_support(1), tri)
+
+
+# ---- decomposition against the definition ------------------------------------------------
+
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_decompose_matches_definition_bruteforce(oracle_mod, h):
+    for seed in range(25):
+        n, edges = random_small(4000 + 17 * h + seed, n_max=7, m_max=10)
+        g = og(oracle_mod, n, edges)
+        t, stamp, _ = g.truss_decompose(h)
+        np.testing.assert_array_equal(t, pins.truss_by_definition(n, edges, h))
+
+
+CLOSED = [("complete", s) for s in (2, 3, 4, 5, 7)] + \
+         [("star", s) for s in (1, 2, 3, 6)] + \
+         [("path", p) for p in (2, 3, 4, 5, 6, 9)] + \
+         [("cycle", p) for p in (3, 4, 5, 6, 7, 8, 11)] + \
+         [("bipartite", ab) for ab in ((1, 3), (2, 2), (2, 3), (3, 4))]
+
+
+@pytest.mark.parametrize("family,size", CLOSED)
+@pytest.mark.parametrize("h", [1, 2, 3, 4])
+def test_closed_forms(oracle_mod, family, size, h):
+    build = {"complete": pins.complete, "star": pins.star, "path": pins.path,
+             "cycle": pins.cycle,
+             "bipartite": lambda ab: pins.complete_bipartite(*ab)}[family]
+    edges = sorted(build(size))
+    n = 1 + max(max(e) for e in edges)
+    g = og(oracle_mod, n, edges)
+    t, _, _ = g.truss_decompose(h)
+    assert set(t.tolist()) == {pins.closed_form_truss(family, size, h)}
+
+
+def test_disjoint_union_decomposes_componentwise(oracle_mod):
+    parts = [pins.complete(5), pins.cycle(9), pins.star(4), pins.path(6)]
+    for h in (1, 2, 3):
+        edges, off, expect = [], 0, []
+        for p in parts:
+            pn = 1 + max(max(e) for e in p)
+            edges += [(u + off, v + off) for u, v in sorted(p)]
+            expect += og(oracle_mod, pn, sorted(p)).truss_decompose(h)[0].tolist()
+            off += pn
+        t, _, _ = og(oracle_mod, off, edges).truss_decompose(h)
+        assert t.tolist() == expect
+
+
+def test_diameter_at_most_h_gives_component_size(oracle_mod):
+    # a wheel (hub + cycle of 8) has diameter 2: every edge gets t = 9 at h = 2
+    edges = sorted(pins.cycle(8)) + [(i, 8) for i in range(8)]
+    edges = sorted((min(a, b), max(a, b)) for a, b in edges)
+    t, _, _ = og(oracle_mod, 9, edges).truss_decompose(2)
+    assert set(t.tolist()) == {9}
+
+
+def test_hand_worked_examples(oracle_mod):
+    seen = 0
+    with open(GOLDEN) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            name, n, h, es, sup, t = [c.strip() for c in line.split("|")]
+            edges = [tuple(int(x) for x in tok.split("-")) for tok in es.split()]
+            g = og(oracle_mod, int(n), edges)
+            assert g.h_support(int(h)).tolist() == [int(x) for x in sup.split()], name
+            assert g.truss_decompose(int(h))[0].tolist() == [int(x) for x in t.split()], name
+            seen += 1
+    assert seen >= 6
+
+
+def test_h1_equals_classic_truss(oracle_mod):
+    for seed in range(12):
+        n = 60
+        s, d = erdos_renyi_gnm(n, 240, 5000 + seed)
+        eu, ev = oracle_mod.normalise(n, s, d)
+        edges = list(zip(eu.tolist(), ev.tolist()))
+        t, _, _ = oracle_mod.OracleGraph(n, eu, ev).truss_decompose(1)
+        np.testing.assert_array_equal(t, pins.classic_truss(n, edges))
+    for seed in range(6):
+        s, d = barabasi_albert(80, 4, 5100 + seed)
+        eu, ev = oracle_mod.normalise(80, s, d)
+        edges = list(zip(eu.tolist(), ev.tolist()))
+        t, _, _ = oracle_mod.OracleGraph(80, eu, ev).truss_decompose(1)
+        np.testing.assert_array_equal(t, pins.classic_truss(80, edges))
+
+
+@pytest.mark.parametrize("h", [1, 2, 3, 4])
+def test_level_synchronous_equals_sequential_algorithm1(oracle_mod, h):
+    for seed in range(8):
+        n = 30
+        s, d = erdos_renyi_gnm(n, 70, 6000 + 10 * h + seed)
+        g = oracle_mod.OracleGraph.from_raw(n, s, d)
+        np.testing.assert_array_equal(g.truss_decompose(h)[0], g.truss_sequential(h))
+    s, d = barabasi_albert(40, 3, 6100 + h)
+    g = oracle_mod.OracleGraph.from_raw(40, s, d)
+    np.testing.assert_array_equal(g.truss_decompose(h)[0], g.truss_sequential(h))
+
+
+def test_invariants_on_corpus(oracle_mod):
+    for n, s, d in small_corpus(30, 77, max_n=40):
+        g = oracle_mod.OracleGraph.from_raw(n, s, d)
+        if g.m == 0:
+            continue
+        prev = None
+        for h in (1, 2, 3, 4):
+            t, stamp, _ = g.truss_decompose(h)
+            sup = g.h_support(h)
+            assert (t >= 2).all()
+            assert (t <= sup + 2).all()  # t <= sup_G + 2
+            # the edges of minimum h-support are peeled first, at k = min sup + 2
+            assert t.min() == sup.min() + 2
+            assert (t[sup == sup.min()] == sup.min() + 2).all()
+            # validity: sup inside T_{t(e)} is at least t(e)-2 (Def. 4 (i))
+            for e in range(g.m):
+                assert g.edge_h_support(h, e, t, int(t[e])) >= t[e] - 2
+            if prev is not None:
+                assert (t >= prev).all()  # monotone non-decreasing in h
+            prev = t
+
+
+def test_relabelling_and_edge_order_invariance(oracle_mod):
+    rng = np.random.default_rng(11)
+    n = 50
+    s, d = erdos_renyi_gnm(n, 160, 7000)
+    base = oracle_mod.OracleGraph.from_raw(n, s, d)
+    for h in (1, 2, 3):
+        t0, _, _ = base.truss_decompose(h)
+        ref = {(int(u), int(v)): int(x) for u, v, x in zip(base.eu, base.ev, t0)}
+        perm = rng.permutation(n).astype(np.int32)
+        order = rng.permutation(s.size)
+        # relabel, shuffle, flip some pairs, add duplicates and self-loops
+        s2 = perm[s][order]
+        d2 = perm[d][order]
+        flip = rng.random(s2.size) < 0.5
+        s2[flip], d2[flip] = d2[flip], s2[flip].copy()
+        s2 = np.concatenate([s2, s2[:20], np.arange(5, dtype=np.int32)])
+        d2 = np.concatenate([d2, d2[:20], np.arange(5, dtype=np.int32)])
+        g2 = oracle_mod.OracleGraph.from_raw(n, s2, d2)
+        t2, _, _ = g2.truss_decompose(h)
+        inv = np.argsort(perm)
+        got = {(min(int(inv[u]), int(inv[v])), max(int(inv[u]), int(inv[v]))): int(x)
+               for u, v, x in zip(g2.eu, g2.ev, t2)}
+        assert got == ref
+
+
+# ---- certificate --------------------------------------------------------------------------
+
+def test_certificate_accepts_oracle_and_rejects_planted_errors(oracle_mod):
+    rng = np.random.default_rng(5)
+    for seed in range(6):
+        s, d = rmat(6, 4, 0.57, 0.19, 0.19, 8000 + seed)
+        g = oracle_mod.OracleGraph.from_raw(64, s, d)
+        for h in (1, 2, 3):
+            t, stamp, _ = g.truss_decompose(h)
+            order_bad, bad, _ = g.certify(h, t, stamp)
+            assert order_bad == 0 and bad.size == 0
+            # planted error 1: one trussness raised by one -> validity or order fails
+            e = int(rng.integers(0, g.m))
+            t1 = t.copy()
+            t1[e] += 1
+            ob, b, _ = g.certify(h, t1, stamp)
+            assert ob > 0 or b.size > 0
+            # planted error 2: one trussness lowered by one -> removability or order fails
+            t2 = t.copy()
+            cand = np.nonzero(t2 > 2)[0]
+            if cand.size:
+                e = int(cand[rng.integers(0, cand.size)])
+                t2[e] -= 1
+                ob, b, _ = g.certify(h, t2, stamp)
+                assert ob > 0 or b.size > 0
+            # planted error 3: an edge stamped as removed later than it was
+            st3 = stamp.copy()
+            e = int(np.argmin(stamp))
+            st3[e] = stamp.max() + 1
+            ob, b, _ = g.certify(h, t, st3)
+            if t[e] < t.max():
+                assert ob > 0 or b.size > 0
+
+
+def test_oracle_finishes_small_workload_quickly(oracle_mod):
+    # a quarter-size version of the 2,000-vertex ER workload must finish in well under
+    # a second; the full one is exercised by the GPU parity tests
+    s, d = erdos_renyi_gnm(500, 2000, 9000)
+    g = oracle_mod.OracleGraph.from_raw(500, s, d)
+    t, stamp, rounds = g.truss_decompose(2)
+    assert rounds > 0 and (t >= 2).all()
