@@ -1,0 +1,152 @@
+/*
+ * htruss.h -- C ABI of the GB300 (sm_103a) higher-order (k,h)-truss decomposition library.
+ *
+ * Method: Chen, Qian, Luo, Li, Wang, "Parallel Higher-order Truss Decomposition" (2024).
+ *   - h-hop neighbourhood N_G(v,h): vertices within distance h of v (Sec. 2);
+ *   - h-support sup_G(e,h) = |N_G(u,h) ∩ N_G(v,h)| for e = (u,v) (Def. 2, Def. 3);
+ *   - (k,h)-truss and h-trussness t(e,h) (Def. 4), computed by peeling (Sec. 3, Lemma 1,
+ *     Algorithm 1), here level-synchronously: every edge of the current level is removed
+ *     in one round, and h-support is recomputed only for edges whose endpoints' h-hop
+ *     balls shrank.
+ * Readings fixed by this library where the paper is silent:
+ *   - a subgraph is an edge set and distances inside it use only its edges;
+ *   - paths through e itself count towards sup(e,h); u and v are not counted;
+ *   - self-loops are dropped, duplicate and reverse pairs merged;
+ *   - edge id = rank of (u,v), u < v, in lexicographic order; outputs are per edge id;
+ *   - t(e,h) >= 2 for every edge (the 2-truss is the whole graph).
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev are device pointers of the current CUDA device; *_host are host
+ *     pointers (pinned memory makes the copies faster but is not required).
+ *   - The caller owns every input and output buffer.  The library owns the graph handle
+ *     and all scratch memory it allocates (stream-ordered, on the device of the call).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is ordered after
+ *     prior work on `stream`; every call below returns only after its results are
+ *     complete and visible on `stream` (the calls synchronise internally).
+ *   - On error nothing is written to the outputs; the handle stays valid unless stated.
+ *   - Errors: HTD_EINVAL (bad argument: NULL pointer, h outside [1, HTD_MAX_H], n < 0,
+ *     vertex id outside [0,n)), HTD_ENOMEM (device allocation failed), HTD_ECUDA (a CUDA
+ *     call failed; htd_last_error() has the message), HTD_EOVERFLOW (2*m_in >= 2^31),
+ *     HTD_EUNSUPPORTED (n > HTD_MAX_N), HTD_ETIMEOUT (the peel exceeded its round cap).
+ *   - Functions are thread-safe for distinct handles; one handle must not be used by two
+ *     threads at once.
+ */
+#ifndef HTRUSS_H
+#define HTRUSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HTD_MAX_H 8          /* largest hop threshold h accepted */
+#define HTD_MAX_N 1600000    /* largest vertex count: an h-hop ball must fit in shared memory as an n-bit set */
+
+typedef enum htd_status {
+    HTD_OK = 0,
+    HTD_EINVAL = 1,
+    HTD_ENOMEM = 2,
+    HTD_ECUDA = 3,
+    HTD_ETIMEOUT = 4,
+    HTD_EOVERFLOW = 5,
+    HTD_EUNSUPPORTED = 6
+} htd_status;
+
+/* Opaque handle: the normalised graph in CSR form on one device plus cached scratch. */
+typedef struct htd_graph htd_graph;
+
+/* Counters of one decomposition (all zero for calls that do not peel). */
+typedef struct htd_stats {
+    int64_t rounds;          /* removal rounds (each removes every edge of the current level) */
+    int64_t levels;          /* distinct k at which edges were removed */
+    int32_t max_truss;       /* largest t(e,h) */
+    int32_t h;
+    int64_t hsup_evals;      /* h-support evaluations: m (initial) + recomputations */
+    int64_t ball_builds;     /* h-hop balls built: n (initial) + rebuilt candidates */
+    int64_t balls_changed;   /* rebuilt balls that had shrunk */
+    int64_t frontier_edges;  /* edges removed (= m at the end) */
+    double alg_bytes_ball;   /* algorithmic bytes of the ball builds (see DESIGN notes) */
+    double alg_bytes_hsup;   /* algorithmic bytes of the h-support intersections */
+    float ms_ball;           /* device time in ball-build launches (timing option only) */
+    float ms_hsup;           /* device time in h-support launches (timing option only) */
+    int64_t launches_ball;   /* ball-build launches (timing option only) */
+    int64_t launches_hsup;   /* h-support launches (timing option only) */
+    int64_t kernel_launches; /* kernels this library launched for the call */
+    int64_t ball_pool_bytes; /* device bytes held by the h-hop balls */
+} htd_stats;
+
+/* Option flags for htd_truss_decompose_ex. */
+#define HTD_OPT_TIMING 1u    /* time ball-build and h-support launches with CUDA events */
+#define HTD_OPT_NO_GRAPH 2u  /* launch each peel round directly instead of via a CUDA graph */
+
+/* Normalise an undirected edge list and build the graph (Sec. 2 graph model).
+ *   n            vertex count, ids in [0, n); 0 <= n <= HTD_MAX_N.
+ *   src, dst     m_in int32 endpoints each (device pointers if inputs_on_device != 0,
+ *                else host pointers); pairs may repeat, appear reversed or be loops.
+ *   out          receives the new handle (set to NULL on error).
+ * Builds: row offsets (n+1), sorted neighbour lists (2m), slot -> edge id (2m) and the
+ * canonical edge list (eu < ev, m edges, lexicographic).  Errors: EINVAL for an id
+ * outside [0,n), EOVERFLOW if 2*m_in >= 2^31, EUNSUPPORTED if n > HTD_MAX_N. */
+htd_status htd_build_csr(int32_t n, const int32_t *src, const int32_t *dst, int64_t m_in,
+                         int inputs_on_device, void *stream, htd_graph **out);
+
+/* Vertex and edge counts of a handle. */
+htd_status htd_graph_info(const htd_graph *g, int32_t *n, int64_t *m);
+
+/* Canonical edges: eu_dev[e] < ev_dev[e], e in [0, m), lexicographic order (device
+ * buffers of m int32 each). */
+htd_status htd_edges(const htd_graph *g, int32_t *eu_dev, int32_t *ev_dev, void *stream);
+
+/* CSR of the normalised graph: row_ptr_dev (n+1), col_dev (2m, neighbours sorted within
+ * each row), slot_eid_dev (2m, edge id of each adjacency slot).  Any pointer may be NULL
+ * to skip that array. */
+htd_status htd_csr(const htd_graph *g, int32_t *row_ptr_dev, int32_t *col_dev,
+                   int32_t *slot_eid_dev, void *stream);
+
+/* h-support of every edge (Def. 2, Def. 3; the parallel loop of Algorithm 2, lines 1-3):
+ * sup_dev[e] = |N(u,h) ∩ N(v,h)| in the whole graph, u and v excluded.
+ * sup_dev: device buffer of m int32.  1 <= h <= HTD_MAX_H. */
+htd_status htd_h_support(htd_graph *g, int32_t h, int32_t *sup_dev, void *stream);
+
+/* (k,h)-truss decomposition (Def. 4; Sec. 3 peeling): truss_dev[e] = t(e,h) for every
+ * edge id (device buffer of m int32, values in [2, n]).
+ *   stamp_dev  nullable device buffer of m int32: the 0-based round in which e was
+ *              removed (rounds are level-synchronous; usable for a peeling certificate).
+ *   stats      nullable host struct, filled on success. */
+htd_status htd_truss_decompose(htd_graph *g, int32_t h, int32_t *truss_dev,
+                               int32_t *stamp_dev, htd_stats *stats, void *stream);
+
+/* Same as htd_truss_decompose with option flags (HTD_OPT_*). */
+htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags,
+                                  int32_t *truss_dev, int32_t *stamp_dev,
+                                  htd_stats *stats, void *stream);
+
+/* End-to-end call on host buffers: copies src/dst (m_in each) to the device, builds the
+ * graph, decomposes it at hop threshold h and copies the canonical edges and t(e,h) back.
+ *   eu_host, ev_host, truss_host  host buffers with room for m_in int32 each; the first
+ *                                 *m_out entries are written.
+ *   m_out                         receives m, the number of distinct edges. */
+htd_status htd_truss_decompose_host(int32_t n, const int32_t *src_host,
+                                    const int32_t *dst_host, int64_t m_in, int32_t h,
+                                    int32_t *eu_host, int32_t *ev_host, int32_t *truss_host,
+                                    int64_t *m_out, htd_stats *stats, void *stream);
+
+/* Frees the handle and every device buffer it owns (NULL is ignored). */
+void htd_graph_free(htd_graph *g);
+
+/* Kernels this library has launched from the calling thread since it was loaded (a
+ * diagnostic counter; graph launches count every kernel node they contain). */
+int64_t htd_kernel_launch_count(void);
+
+/* Static description of a status code. */
+const char *htd_status_string(htd_status s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *htd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HTRUSS_H */

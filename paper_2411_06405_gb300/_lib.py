@@ -1,0 +1,108 @@
+"""ctypes view of libhtruss.so (include/htruss.h).  Argument marshalling only."""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libhtruss.so")
+
+HTD_OK = 0
+HTD_EINVAL = 1
+HTD_ENOMEM = 2
+HTD_ECUDA = 3
+HTD_ETIMEOUT = 4
+HTD_EOVERFLOW = 5
+HTD_EUNSUPPORTED = 6
+HTD_MAX_H = 8
+HTD_MAX_N = 1600000
+HTD_OPT_TIMING = 1
+HTD_OPT_NO_GRAPH = 2
+
+# every symbol include/htruss.h declares
+EXPORTED = (
+    "htd_build_csr", "htd_graph_info", "htd_edges", "htd_csr", "htd_h_support",
+    "htd_truss_decompose", "htd_truss_decompose_ex", "htd_truss_decompose_host",
+    "htd_graph_free", "htd_kernel_launch_count", "htd_status_string", "htd_last_error",
+)
+
+
+class HtdStats(ctypes.Structure):
+    _fields_ = [
+        ("rounds", ctypes.c_int64),
+        ("levels", ctypes.c_int64),
+        ("max_truss", ctypes.c_int32),
+        ("h", ctypes.c_int32),
+        ("hsup_evals", ctypes.c_int64),
+        ("ball_builds", ctypes.c_int64),
+        ("balls_changed", ctypes.c_int64),
+        ("frontier_edges", ctypes.c_int64),
+        ("alg_bytes_ball", ctypes.c_double),
+        ("alg_bytes_hsup", ctypes.c_double),
+        ("ms_ball", ctypes.c_float),
+        ("ms_hsup", ctypes.c_float),
+        ("launches_ball", ctypes.c_int64),
+        ("launches_hsup", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
+        ("ball_pool_bytes", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class HtdError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: status {status}: {message}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Loads the compiled library; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with paper_2411_06405_gb300.build.build() "
+                "(there is no CPU fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        i32, i64, u32, p = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        ps = ctypes.POINTER(HtdStats)
+        sig = {
+            "htd_build_csr": ([i32, p, p, i64, ctypes.c_int, p, pp], ctypes.c_int),
+            "htd_graph_info": ([p, ctypes.POINTER(i32), ctypes.POINTER(i64)], ctypes.c_int),
+            "htd_edges": ([p, p, p, p], ctypes.c_int),
+            "htd_csr": ([p, p, p, p, p], ctypes.c_int),
+            "htd_h_support": ([p, i32, p, p], ctypes.c_int),
+            "htd_truss_decompose": ([p, i32, p, p, ps, p], ctypes.c_int),
+            "htd_truss_decompose_ex": ([p, i32, u32, p, p, ps, p], ctypes.c_int),
+            "htd_truss_decompose_host": ([i32, p, p, i64, i32, p, p, p, ctypes.POINTER(i64), ps, p],
+                                         ctypes.c_int),
+            "htd_graph_free": ([p], None),
+            "htd_kernel_launch_count": ([], i64),
+            "htd_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "htd_last_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def check(status: int, where: str):
+    if status != HTD_OK:
+        lib = load()
+        msg = lib.htd_last_error().decode(errors="replace")
+        base = lib.htd_status_string(status).decode(errors="replace")
+        raise HtdError(status, where, f"{base}: {msg}")

@@ -1,0 +1,89 @@
+// htd_internal.h -- host-side structures shared by the translation units of libhtruss.
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/htruss.h"
+#include "htd_common.cuh"
+
+namespace htd {
+
+// Normalised graph on one device (Sec. 2 graph model, CSR form).
+struct GraphDev {
+    int device = 0;
+    int32_t n = 0;
+    int64_t m = 0;
+    int32_t *row_ptr = nullptr;   // n+1
+    int32_t *col = nullptr;       // 2m, sorted within each row
+    int32_t *slot_eid = nullptr;  // 2m, edge id of each slot
+    int32_t *eu = nullptr;        // m, eu < ev
+    int32_t *ev = nullptr;        // m
+    int32_t *slot_lo = nullptr;   // m, slot of ev[e] in row eu[e]
+    int32_t *slot_hi = nullptr;   // m, slot of eu[e] in row ev[e]
+};
+
+// Device scratch of one h-support pass / peel, cached on the handle between calls.
+struct PeelWork {
+    int32_t h = 0;
+    int32_t W = 0;                 // 32-bit words of an n-bit set
+    int32_t Wpad = 0;              // W rounded up to a multiple of 4
+    int64_t pool_words = 0;        // ball storage size (uint32 words)
+    uint32_t *pool = nullptr;      // ball storage
+    int64_t *ball_off = nullptr;   // n+1 offsets into pool (multiples of 4 words)
+    int32_t *ball_need = nullptr;  // n storage words of the initial balls
+    int32_t *ball_size = nullptr;  // n members of each ball (the vertex itself included)
+    int32_t *ball_nw = nullptr;    // n: -1 = dense (W words), else (index,bits) pair count
+    int32_t *col_live = nullptr;   // 2m neighbour ids, ~id once the edge is removed
+    int32_t *deg_alive = nullptr;  // n alive degrees
+    int32_t *sup = nullptr;        // m h-support (INT_MAX once removed)
+    int32_t *truss = nullptr;      // m (points at the caller's output during a peel)
+    int32_t *stamp = nullptr;      // m
+    int32_t *frontier = nullptr;   // m
+    int32_t *cand_list = nullptr;  // n
+    int32_t *cand_stamp = nullptr; // n round of the last candidate mark
+    int32_t *changed_list = nullptr;   // n
+    int32_t *changed_stamp = nullptr;  // n round in which the ball last shrank
+    int2 *items = nullptr;         // (vertex, first slot) h-support work items
+    int64_t items_cap = 0;
+    int32_t *bfs_lists = nullptr;  // per-block BFS level lists (h >= 3)
+    int64_t bfs_list_len = 0;      // entries per list
+    void *scan_tmp = nullptr;
+    DevStatus *status = nullptr;
+    DevStatus *status_host = nullptr;  // pinned mirror
+    int grid_ball = 0;             // persistent grid sizes
+    int grid_hsup = 0;
+    int grid_edges = 0;
+    size_t smem_ball = 0;
+    size_t smem_hsup = 0;
+};
+
+struct Handle {
+    GraphDev g;
+    PeelWork w;
+    cudaStream_t pstream = nullptr;       // private stream (graph capture needs one)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph_exec = nullptr; // cached round graph
+    int graph_h = 0;
+    int graph_rounds = 0;
+    int32_t *graph_truss = nullptr, *graph_stamp = nullptr;
+    int num_sms = 0;
+};
+
+void set_last_error(const std::string &msg);
+
+// CSR builder (htd_csr.cu).  src/dst are device pointers.
+htd_status build_csr_device(int32_t n, const int32_t *src, const int32_t *dst, int64_t m_in,
+                            cudaStream_t s, GraphDev *out, int64_t *launches);
+void free_graph_dev(GraphDev *g);
+
+// Ball builder, h-support and peel rounds (htd_peel.cu).
+htd_status ensure_work(Handle *H, int32_t h);
+void free_work(PeelWork *w);
+htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
+                        htd_stats *timing);
+htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t *evs);
+
+}  // namespace htd

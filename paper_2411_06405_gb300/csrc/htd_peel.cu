@@ -1,0 +1,845 @@
+// htd_peel.cu -- h-hop balls, h-support and level-synchronous peeling on the device.
+//
+// Notation (Sec. 2): B(x,h) = x plus every vertex within distance h of x over the alive
+// edges, so N(x,h) = B(x,h) \ {x} and, for an alive edge e = (u,v),
+//     sup(e,h) = |N(u,h) ∩ N(v,h)| = |B(u,h) ∩ B(v,h)| - 2            (Def. 2, Def. 3)
+// because u and v lie in both balls.
+//
+// Balls are materialised per vertex as n-bit sets, stored either dense (W words) or as a
+// sorted list of (word index, word) pairs when that is at most W words; the choice is
+// remade at every rebuild and always fits the storage reserved by the first build,
+// because balls only shrink as edges are removed.
+//
+// One peel round (Sec. 3, Algorithm 1 with every edge of level k removed together):
+//   select     F = alive edges with sup <= k-2 (k = max(k, min alive sup + 2));
+//   candidates vertices within distance h-1 of an endpoint of F, before removal: only
+//              their balls can lose members (a lost shortest path of length <= h runs
+//              through a removed edge, so its start is within h-1 of that edge);
+//   remove     t(e) = k, stamp(e) = round, the edge's two adjacency slots are marked dead;
+//   rebuild    every candidate's ball; a ball that shrank marks its vertex "changed";
+//   recompute  sup(e) for every alive edge with a changed endpoint (sup depends only on
+//              the two balls), owned by one endpoint so each edge is computed once;
+//   reduce     min alive sup and alive count; the host polls them between graph launches.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "htd_internal.h"
+#include "htd_scan.cuh"
+
+namespace htd {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kNWarps = kBlock / 32;
+constexpr int kItemChunk = 64;  // adjacency slots per h-support work item
+
+enum BallMode { kModeCount = 0, kModeStore = 1, kModeRebuild = 2 };
+
+struct BallArgs {
+    int32_t n, W, Wpad, h;
+    int32_t count_bytes;
+    const int32_t *row_ptr;
+    const int32_t *col_live;
+    const int32_t *deg_alive;
+    uint32_t *pool;
+    const int64_t *ball_off;
+    int32_t *ball_need;
+    int32_t *ball_size;
+    int32_t *ball_nw;
+    const int32_t *cand_list;
+    int32_t *changed_list;
+    int32_t *changed_stamp;
+    int32_t *bfs_lists;
+    int64_t bfs_list_len;
+    DevStatus *st;
+};
+
+// Sets bit z of the block's n-bit set; returns true if this thread set it first.
+__device__ __forceinline__ bool set_member(uint32_t *bits, int32_t z) {
+    const uint32_t m = 1u << (z & 31);
+    uint32_t *w = bits + (z >> 5);
+    if (*(volatile uint32_t *)w & m) return false;
+    return (atomicOr(w, m) & m) == 0u;
+}
+
+// Load-balanced expansion of up to kBlock frontier vertices (one per thread, -1 = none):
+// every alive neighbour z of them is set in `bits`; if `next` is non-null, vertices set
+// for the first time are appended to it.  Consecutive threads read consecutive slots.
+__device__ __forceinline__ void expand_chunk(int32_t y, const int32_t *__restrict__ row_ptr,
+                                             const int32_t *__restrict__ col_live,
+                                             uint32_t *bits, int32_t *s_off, int32_t *s_beg,
+                                             int32_t *s_scan, int32_t *next,
+                                             int32_t *next_cnt) {
+    int beg = 0, len = 0;
+    if (y >= 0) {
+        beg = row_ptr[y];
+        len = row_ptr[y + 1] - beg;
+    }
+    int total;
+    const int off = block_exclusive_scan<kBlock, int>(len, &total, s_scan);
+    s_off[threadIdx.x] = off;
+    s_beg[threadIdx.x] = beg;
+    __syncthreads();
+    for (int t = threadIdx.x; t < total; t += kBlock) {
+        int lo = 0, hi = kBlock - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const int z = col_live[s_beg[lo] + (t - s_off[lo])];
+        bool fresh = false;
+        if (z >= 0) fresh = set_member(bits, z);
+        if (next) warp_append(fresh, z, next_cnt, next);
+    }
+    __syncthreads();
+}
+
+// Builds B(x,h) for a list of vertices, one vertex per block at a time (work queue).
+//   kModeCount:   records the storage words the ball needs (first pass);
+//   kModeStore:   stores the ball at its reserved offset (second pass);
+//   kModeRebuild: rebuilds a peel candidate; stores it and marks x changed iff it shrank.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock) k_ball(BallArgs a) {
+    extern __shared__ __align__(16) uint32_t bits[];
+    __shared__ int32_t s_scan[kNWarps];
+    __shared__ int32_t s_off[kBlock], s_beg[kBlock];
+    __shared__ int32_t s_item;
+    __shared__ int32_t s_cnt[2];
+    __shared__ int32_t s_wsz[kNWarps], s_wnz[kNWarps];
+    __shared__ unsigned long long s_bytes;
+
+    DevStatus *st = a.st;
+    int count;
+    int32_t *queue;
+    if (MODE == kModeRebuild) {
+        if (st->alive == 0) return;
+        count = 0;
+        for (int j = 0; j < a.h && j < kMaxH; j++) count += st->cand_cnt[j];
+        queue = &st->q_ball;
+    } else {
+        count = a.n;
+        queue = (MODE == kModeCount) ? &st->q_count : &st->q_store;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int W = a.W;
+    const int seg = ((W + kNWarps - 1) / kNWarps + 31) & ~31;
+    int32_t *lists[2] = {nullptr, nullptr};
+    if (a.h >= 3) {
+        lists[0] = a.bfs_lists + (int64_t)blockIdx.x * 2 * a.bfs_list_len;
+        lists[1] = lists[0] + a.bfs_list_len;
+    }
+    if (threadIdx.x == 0) s_bytes = 0ull;
+    unsigned long long bytes = 0ull;  // per-thread share of the algorithmic bytes
+
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= count) break;
+        const int x = (MODE == kModeRebuild) ? a.cand_list[it] : it;
+
+        uint4 *bits4 = reinterpret_cast<uint4 *>(bits);
+        for (int i = threadIdx.x; i < (a.Wpad >> 2); i += kBlock) bits4[i] = make_uint4(0, 0, 0, 0);
+        if (threadIdx.x == 0) {
+            s_cnt[0] = 0;
+            s_cnt[1] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            atomicOr(&bits[x >> 5], 1u << (x & 31));
+            if (a.count_bytes && a.h >= 2) bytes += 8ull + 4ull * (unsigned)a.deg_alive[x];
+        }
+        // depth 1 (x's alive neighbours) and depth 2 (their neighbours)
+        const int rb = a.row_ptr[x], re = a.row_ptr[x + 1];
+        for (int c = rb; c < re; c += kBlock) {
+            const int s = c + threadIdx.x;
+            int y = -1;
+            if (s < re) {
+                y = a.col_live[s];
+                if (y < 0) y = -1;
+            }
+            if (y >= 0) {
+                set_member(bits, y);
+                if (a.count_bytes && a.h >= 2) bytes += 8ull + 4ull * (unsigned)a.deg_alive[y];
+            }
+            if (a.h >= 2) {
+                expand_chunk(y, a.row_ptr, a.col_live, bits, s_off, s_beg, s_scan,
+                             a.h >= 3 ? lists[0] : nullptr, &s_cnt[0]);
+            }
+        }
+        // depth 3..h from the level lists
+        for (int d = 3; d <= a.h; d++) {
+            const int cur = (d - 3) & 1, nxt = cur ^ 1;
+            __syncthreads();
+            const int ncur = s_cnt[cur];
+            __syncthreads();
+            if (threadIdx.x == 0) s_cnt[nxt] = 0;
+            __syncthreads();
+            for (int c = 0; c < ncur; c += kBlock) {
+                const int i = c + threadIdx.x;
+                const int y = (i < ncur) ? lists[cur][i] : -1;
+                if (a.count_bytes && y >= 0) bytes += 8ull + 4ull * (unsigned)a.deg_alive[y];
+                expand_chunk(y, a.row_ptr, a.col_live, bits, s_off, s_beg, s_scan,
+                             d < a.h ? lists[nxt] : nullptr, &s_cnt[nxt]);
+            }
+        }
+        __syncthreads();
+
+        // ball size and non-zero words, per warp segment of words
+        const int w0 = wid * seg, w1 = min(W, w0 + seg);
+        int sz = 0, nz = 0;
+        for (int i = w0 + lane; i < w1; i += 32) {
+            const uint32_t w = bits[i];
+            sz += __popc(w);
+            nz += (w != 0u);
+        }
+        sz = warp_sum(sz);
+        nz = warp_sum(nz);
+        if (lane == 0) {
+            s_wsz[wid] = sz;
+            s_wnz[wid] = nz;
+        }
+        __syncthreads();
+        int size = 0, nzw = 0, wbase = 0;
+#pragma unroll
+        for (int j = 0; j < kNWarps; j++) {
+            size += s_wsz[j];
+            nzw += s_wnz[j];
+            if (j < wid) wbase += s_wnz[j];
+        }
+        const bool dense = 2 * nzw > W;
+        const int stor = dense ? a.Wpad : ((2 * nzw + 3) & ~3);
+        bool store = true;
+        if (MODE == kModeCount) {
+            if (threadIdx.x == 0) a.ball_need[x] = stor;
+            store = false;
+        } else if (MODE == kModeRebuild) {
+            const int old = a.ball_size[x];
+            if (size == old) store = false;
+            else if (size > old) {
+                if (threadIdx.x == 0) atomicOr(&st->err, kErrBallGrew);
+                store = false;
+            }
+        }
+        if (store) {
+            const int64_t off = a.ball_off[x];
+            const int64_t cap = a.ball_off[x + 1] - off;
+            if (stor > cap) {
+                if (threadIdx.x == 0) atomicOr(&st->err, kErrBallCapacity);
+            } else if (dense) {
+                uint4 *dst = reinterpret_cast<uint4 *>(a.pool + off);
+                for (int i = threadIdx.x; i < (a.Wpad >> 2); i += kBlock) dst[i] = bits4[i];
+            } else {
+                uint2 *dst = reinterpret_cast<uint2 *>(a.pool + off);
+                int run = wbase;
+                for (int i0 = w0; i0 < w1; i0 += 32) {
+                    const int i = i0 + lane;
+                    const uint32_t w = (i < w1) ? bits[i] : 0u;
+                    const unsigned bal = __ballot_sync(0xffffffffu, w != 0u);
+                    if (w != 0u) dst[run + __popc(bal & lanemask_lt())] = make_uint2((uint32_t)i, w);
+                    run += __popc(bal);
+                }
+            }
+            if (threadIdx.x == 0 && stor <= cap) {
+                a.ball_size[x] = size;
+                a.ball_nw[x] = dense ? -1 : nzw;
+                if (MODE == kModeRebuild) {
+                    a.changed_stamp[x] = st->round;
+                    a.changed_list[atomicAdd(&st->nchanged, 1)] = x;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (a.count_bytes) {
+        unsigned long long b = bytes;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+        if (lane == 0 && b) atomicAdd(&s_bytes, b);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_bytes) atomicAdd(&st->st_bytes_ball, s_bytes);
+    }
+}
+
+struct HsupArgs {
+    int32_t n, W, Wpad;
+    int32_t initial;
+    int32_t count_bytes;
+    const int32_t *row_ptr;
+    const int32_t *col_live;
+    const int32_t *slot_eid;
+    const uint32_t *pool;
+    const int64_t *ball_off;
+    const int32_t *ball_size;
+    const int32_t *ball_nw;
+    const int32_t *changed_stamp;
+    const int2 *items;
+    int32_t *sup;
+    DevStatus *st;
+};
+
+// h-support of the edges of each work item (vertex x, run of x's adjacency slots).  The
+// block loads B(x,h) into shared memory as a dense set; each warp takes one slot, and if
+// x owns the edge it streams the other endpoint's stored ball against it:
+//   sup(e) = popc(B(x) & B(y)) - 2.
+// Ownership: x owns (x,y) if y's ball did not change this round, else the endpoint with
+// the larger stored ball owns it (ties: smaller id).  In the initial pass every ball
+// counts as changed, so each edge is computed exactly once.
+__global__ void __launch_bounds__(kBlock) k_hsup(HsupArgs a) {
+    extern __shared__ __align__(16) uint32_t bits[];
+    __shared__ int32_t s_item;
+    __shared__ unsigned long long s_bytes;
+    __shared__ int32_t s_owned;
+    DevStatus *st = a.st;
+    if (!a.initial && st->alive == 0) return;
+    const int nitems = st->nitems;
+    const int round = st->round;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int W = a.W;
+    uint4 *bits4 = reinterpret_cast<uint4 *>(bits);
+    const uint4 *pool4 = reinterpret_cast<const uint4 *>(a.pool);
+    const uint2 *pool2 = reinterpret_cast<const uint2 *>(a.pool);
+    if (threadIdx.x == 0) {
+        s_bytes = 0ull;
+        s_owned = 0;
+    }
+    unsigned long long bytes = 0ull;
+    int owned = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&st->q_items, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const int2 item = a.items[it];
+        const int x = item.x;
+        const int nwx = a.ball_nw[x];
+        const int64_t offx = a.ball_off[x];
+        if (nwx < 0) {
+            for (int i = threadIdx.x; i < (a.Wpad >> 2); i += kBlock) bits4[i] = pool4[(offx >> 2) + i];
+        } else {
+            for (int i = threadIdx.x; i < (a.Wpad >> 2); i += kBlock) bits4[i] = make_uint4(0, 0, 0, 0);
+            __syncthreads();
+            for (int j = threadIdx.x; j < nwx; j += kBlock) {
+                const uint2 p = pool2[(offx >> 1) + j];
+                bits[p.x] = p.y;
+            }
+        }
+        __syncthreads();
+        const int storx = nwx < 0 ? W : 2 * nwx;
+        const int s1 = min(a.row_ptr[x + 1], item.y + kItemChunk);
+        for (int s = item.y + wid; s < s1; s += kNWarps) {
+            const int y = a.col_live[s];
+            if (y < 0) continue;
+            const bool ychanged = a.initial || a.changed_stamp[y] == round;
+            const int nwy = a.ball_nw[y];
+            const int story = nwy < 0 ? W : 2 * nwy;
+            const bool own = !ychanged || storx > story || (storx == story && x < y);
+            if (!own) continue;
+            const int64_t offy = a.ball_off[y];
+            int cnt = 0;
+            if (nwy < 0) {
+                const uint4 *p = pool4 + (offy >> 2);
+                for (int i = lane; i < (a.Wpad >> 2); i += 32) {
+                    const uint4 v = p[i];
+                    const uint4 b = bits4[i];
+                    cnt += __popc(v.x & b.x) + __popc(v.y & b.y) + __popc(v.z & b.z) +
+                           __popc(v.w & b.w);
+                }
+            } else {
+                const uint2 *p = pool2 + (offy >> 1);
+                for (int j = lane; j < nwy; j += 32) {
+                    const uint2 v = p[j];
+                    cnt += __popc(bits[v.x] & v.y);
+                }
+            }
+            cnt = warp_sum(cnt);
+            if (lane == 0) {
+                a.sup[a.slot_eid[s]] = cnt - 2;
+                owned++;
+                if (a.count_bytes)
+                    bytes += 4ull * (unsigned)(story) + 12ull;
+            }
+        }
+        if (a.count_bytes && threadIdx.x == 0) bytes += 4ull * (unsigned)storx;
+        __syncthreads();
+    }
+    if (lane == 0 && owned) atomicAdd(&s_owned, owned);
+    if (a.count_bytes) {
+        unsigned long long b = bytes;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+        if (lane == 0 && b) atomicAdd(&s_bytes, b);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (a.count_bytes && s_bytes) atomicAdd(&st->st_bytes_hsup, s_bytes);
+        if (!a.initial && s_owned) atomicAdd((unsigned long long *)&st->st_recomputed,
+                                             (unsigned long long)s_owned);
+    }
+}
+
+// Work items for k_hsup: every vertex of `list` (all vertices if list is null) gets one
+// item per kItemChunk adjacency slots.  One atomic per warp.
+__global__ void k_make_items(const int32_t *__restrict__ list, int32_t initial, int32_t n,
+                             const int32_t *__restrict__ row_ptr, int2 *__restrict__ items,
+                             DevStatus *st) {
+    if (!initial && st->alive == 0) return;
+    const int count = list ? st->nchanged : n;
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < count; i0 += stride) {
+        const int i = i0 + lane;
+        int x = -1, rb = 0, nch = 0;
+        if (i < count) {
+            x = list ? list[i] : i;
+            rb = row_ptr[x];
+            nch = (row_ptr[x + 1] - rb + kItemChunk - 1) / kItemChunk;
+        }
+        int incl = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        int base = 0;
+        if (lane == 31 && tot) base = atomicAdd(&st->nitems, tot);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        const int first = base + incl - nch;
+        for (int c = 0; c < nch; c++) items[first + c] = make_int2(x, rb + c * kItemChunk);
+    }
+}
+
+__global__ void k_select(const int32_t *__restrict__ sup, int64_t m, DevStatus *st,
+                         int32_t *__restrict__ frontier) {
+    if (st->alive == 0) return;
+    const int thr = st->k - 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); e0 < m; e0 += stride) {
+        const int64_t e = e0 + (threadIdx.x & 31);
+        const bool p = e < m && sup[e] <= thr;
+        warp_append(p, (int32_t)e, &st->nF, frontier);
+    }
+}
+
+__device__ __forceinline__ void cand_mark(bool pred, int32_t w, int round, int level,
+                                          int base, int32_t *cand_stamp, int32_t *cand_list,
+                                          DevStatus *st) {
+    bool fresh = pred && atomicExch(&cand_stamp[w], round) != round;
+    warp_append(fresh, w, &st->cand_cnt[level], cand_list + base);
+}
+
+// Depth 0 of the candidate search: both endpoints of every frontier edge.
+__global__ void k_cand_init(const int32_t *__restrict__ frontier, const int32_t *__restrict__ eu,
+                            const int32_t *__restrict__ ev, DevStatus *st,
+                            int32_t *__restrict__ cand_stamp, int32_t *__restrict__ cand_list) {
+    if (st->alive == 0) return;
+    const int nF = st->nF, round = st->round;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < nF; i0 += stride) {
+        const int i = i0 + (threadIdx.x & 31);
+        const bool p = i < nF;
+        const int e = p ? frontier[i] : 0;
+        cand_mark(p, p ? eu[e] : 0, round, 0, 0, cand_stamp, cand_list, st);
+        cand_mark(p, p ? ev[e] : 0, round, 0, 0, cand_stamp, cand_list, st);
+    }
+}
+
+// Depth d of the candidate search (alive edges, frontier still present): one warp per
+// vertex found at depth d-1.
+__global__ void k_cand_expand(int32_t d, const int32_t *__restrict__ row_ptr,
+                              const int32_t *__restrict__ col_live, DevStatus *st,
+                              int32_t *__restrict__ cand_stamp, int32_t *__restrict__ cand_list) {
+    if (st->alive == 0) return;
+    int start = 0;
+    for (int j = 0; j < d - 1; j++) start += st->cand_cnt[j];
+    const int len = st->cand_cnt[d - 1];
+    const int out_base = start + len;
+    const int round = st->round;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < len; i += nwarps) {
+        const int w = cand_list[start + i];
+        const int rb = row_ptr[w], re = row_ptr[w + 1];
+        for (int s0 = rb; s0 < re; s0 += 32) {
+            const int s = s0 + lane;
+            const int z = (s < re) ? col_live[s] : -1;
+            cand_mark(z >= 0, z >= 0 ? z : 0, round, d, out_base, cand_stamp, cand_list, st);
+        }
+    }
+}
+
+__global__ void k_remove(const int32_t *__restrict__ frontier, DevStatus *st,
+                         const int32_t *__restrict__ eu, const int32_t *__restrict__ ev,
+                         const int32_t *__restrict__ slot_lo, const int32_t *__restrict__ slot_hi,
+                         int32_t *__restrict__ sup, int32_t *__restrict__ truss,
+                         int32_t *__restrict__ stamp, int32_t *__restrict__ col_live,
+                         int32_t *__restrict__ deg_alive) {
+    if (st->alive == 0) return;
+    const int nF = st->nF, k = st->k, round = st->round;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
+        const int e = frontier[i];
+        const int u = eu[e], v = ev[e];
+        truss[e] = k;
+        stamp[e] = round;
+        sup[e] = INT_MAX;
+        col_live[slot_lo[e]] = ~v;
+        col_live[slot_hi[e]] = ~u;
+        atomicSub(&deg_alive[u], 1);
+        atomicSub(&deg_alive[v], 1);
+    }
+}
+
+// Minimum alive h-support and alive count; the last block to finish closes the round:
+// bookkeeping, next level k = max(k, min + 2) (Algorithm 1's bins skip empty levels),
+// and reset of the per-round counters.
+__global__ void __launch_bounds__(kBlock) k_minreduce(const int32_t *__restrict__ sup, int64_t m,
+                                                      DevStatus *st, int32_t initial) {
+    __shared__ int32_t s_min[kNWarps];
+    __shared__ long long s_cnt[kNWarps];
+    __shared__ bool s_last;
+    if (!initial && st->alive == 0) return;
+    int lmin = INT_MAX;
+    long long lc = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int s = sup[e];
+        if (s != INT_MAX) {
+            lmin = min(lmin, s);
+            lc++;
+        }
+    }
+    lmin = warp_min(lmin);
+    lc = warp_sum_ll(lc);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_min[wid] = lmin;
+        s_cnt[wid] = lc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int bm = INT_MAX;
+        long long bc = 0;
+        for (int j = 0; j < kNWarps; j++) {
+            bm = min(bm, s_min[j]);
+            bc += s_cnt[j];
+        }
+        if (bm != INT_MAX) atomicMin(&st->min_acc, bm);
+        if (bc) atomicAdd((unsigned long long *)&st->alive_acc, (unsigned long long)bc);
+        __threadfence();
+        const unsigned ticket = atomicAdd(&st->done_blocks, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const int mn = atomicAdd(&st->min_acc, 0);
+        const long long al = (long long)atomicAdd((unsigned long long *)&st->alive_acc, 0ull);
+        const int nF = st->nF;
+        if (!initial && nF > 0) {
+            if (st->k != st->last_k) {
+                st->levels++;
+                st->last_k = st->k;
+            }
+            st->max_k = max(st->max_k, st->k);
+            st->round++;
+            st->st_frontier += nF;
+            int cands = 0;
+            for (int j = 0; j < kMaxH; j++) cands += st->cand_cnt[j];
+            st->st_candidates += cands;
+            st->st_changed += st->nchanged;
+        }
+        st->alive = al;
+        if (al > 0) st->k = max(st->k, mn + 2);
+        st->min_acc = INT_MAX;
+        st->alive_acc = 0;
+        st->done_blocks = 0u;
+        st->nF = 0;
+        for (int j = 0; j < kMaxH; j++) st->cand_cnt[j] = 0;
+        st->nchanged = 0;
+        st->nitems = 0;
+        st->q_ball = 0;
+        st->q_items = 0;
+        __threadfence();
+    }
+}
+
+__global__ void k_init_deg(int32_t n, const int32_t *__restrict__ row_ptr,
+                           int32_t *__restrict__ deg_alive) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
+        deg_alive[x] = row_ptr[x + 1] - row_ptr[x];
+}
+
+#define HTD_CHECK(...)                                                              \
+    do {                                                                             \
+        cudaError_t _e = (__VA_ARGS__);                                                     \
+        if (_e != cudaSuccess) {                                                     \
+            set_last_error(std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(_e));      \
+            return (_e == cudaErrorMemoryAllocation) ? HTD_ENOMEM : HTD_ECUDA;       \
+        }                                                                            \
+    } while (0)
+
+template <typename T>
+cudaError_t alloc_n(T **p, int64_t count) {
+    return cudaMalloc(reinterpret_cast<void **>(p), (size_t)(count > 0 ? count : 1) * sizeof(T));
+}
+
+BallArgs ball_args(Handle *H) {
+    PeelWork &w = H->w;
+    GraphDev &g = H->g;
+    BallArgs a;
+    a.n = g.n;
+    a.W = w.W;
+    a.Wpad = w.Wpad;
+    a.h = w.h;
+    a.count_bytes = 1;
+    a.row_ptr = g.row_ptr;
+    a.col_live = w.col_live;
+    a.deg_alive = w.deg_alive;
+    a.pool = w.pool;
+    a.ball_off = w.ball_off;
+    a.ball_need = w.ball_need;
+    a.ball_size = w.ball_size;
+    a.ball_nw = w.ball_nw;
+    a.cand_list = w.cand_list;
+    a.changed_list = w.changed_list;
+    a.changed_stamp = w.changed_stamp;
+    a.bfs_lists = w.bfs_lists;
+    a.bfs_list_len = w.bfs_list_len;
+    a.st = w.status;
+    return a;
+}
+
+HsupArgs hsup_args(Handle *H, int initial) {
+    PeelWork &w = H->w;
+    GraphDev &g = H->g;
+    HsupArgs a;
+    a.n = g.n;
+    a.W = w.W;
+    a.Wpad = w.Wpad;
+    a.initial = initial;
+    a.count_bytes = 1;
+    a.row_ptr = g.row_ptr;
+    a.col_live = w.col_live;
+    a.slot_eid = g.slot_eid;
+    a.pool = w.pool;
+    a.ball_off = w.ball_off;
+    a.ball_size = w.ball_size;
+    a.ball_nw = w.ball_nw;
+    a.changed_stamp = w.changed_stamp;
+    a.items = w.items;
+    a.sup = w.sup;
+    a.st = w.status;
+    return a;
+}
+
+}  // namespace
+
+void free_work(PeelWork *w) {
+    cudaFree(w->pool);
+    cudaFree(w->ball_off);
+    cudaFree(w->ball_need);
+    cudaFree(w->ball_size);
+    cudaFree(w->ball_nw);
+    cudaFree(w->col_live);
+    cudaFree(w->deg_alive);
+    cudaFree(w->sup);
+    cudaFree(w->truss);
+    cudaFree(w->stamp);
+    cudaFree(w->frontier);
+    cudaFree(w->cand_list);
+    cudaFree(w->cand_stamp);
+    cudaFree(w->changed_list);
+    cudaFree(w->changed_stamp);
+    cudaFree(w->items);
+    cudaFree(w->bfs_lists);
+    cudaFree(w->scan_tmp);
+    cudaFree(w->status);
+    if (w->status_host) cudaFreeHost(w->status_host);
+    *w = PeelWork{};
+}
+
+// Allocates (or reuses) the scratch of an h-support pass / peel at hop threshold h.
+htd_status ensure_work(Handle *H, int32_t h) {
+    PeelWork &w = H->w;
+    GraphDev &g = H->g;
+    if (w.status && w.h == h) return HTD_OK;
+    if (w.status) {
+        // the per-block BFS lists and the ball storage depend on h: rebuild everything
+        free_work(&w);
+    }
+    const int64_t n = g.n, m = g.m;
+    w.h = h;
+    w.W = (int32_t)((n + 31) / 32);
+    if (w.W < 1) w.W = 1;
+    w.Wpad = (w.W + 3) & ~3;
+    w.smem_ball = (size_t)w.Wpad * 4;
+    w.smem_hsup = (size_t)w.Wpad * 4;
+    HTD_CHECK(cudaFuncSetAttribute(k_ball<kModeCount>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)w.smem_ball));
+    HTD_CHECK(cudaFuncSetAttribute(k_ball<kModeStore>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)w.smem_ball));
+    HTD_CHECK(cudaFuncSetAttribute(k_ball<kModeRebuild>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w.smem_ball));
+    HTD_CHECK(cudaFuncSetAttribute(k_hsup, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)w.smem_hsup));
+    int occ_ball = 0, occ_hsup = 0;
+    HTD_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ball, k_ball<kModeRebuild>,
+                                                            kBlock, w.smem_ball));
+    HTD_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_hsup, k_hsup, kBlock,
+                                                            w.smem_hsup));
+    if (occ_ball < 1 || occ_hsup < 1) {
+        set_last_error("htd: an n-bit ball does not fit in shared memory");
+        return HTD_EUNSUPPORTED;
+    }
+    w.grid_ball = H->num_sms * occ_ball;
+    w.grid_hsup = H->num_sms * occ_hsup;
+    w.grid_edges = H->num_sms * 4;
+    HTD_CHECK(alloc_n(&w.ball_off, n + 1));
+    HTD_CHECK(alloc_n(&w.ball_need, n));
+    HTD_CHECK(alloc_n(&w.ball_size, n));
+    HTD_CHECK(alloc_n(&w.ball_nw, n));
+    HTD_CHECK(alloc_n(&w.col_live, 2 * m));
+    HTD_CHECK(alloc_n(&w.deg_alive, n));
+    HTD_CHECK(alloc_n(&w.sup, m));
+    HTD_CHECK(alloc_n(&w.truss, m));
+    HTD_CHECK(alloc_n(&w.stamp, m));
+    HTD_CHECK(alloc_n(&w.frontier, m));
+    HTD_CHECK(alloc_n(&w.cand_list, n));
+    HTD_CHECK(alloc_n(&w.cand_stamp, n));
+    HTD_CHECK(alloc_n(&w.changed_list, n));
+    HTD_CHECK(alloc_n(&w.changed_stamp, n));
+    w.items_cap = n + (2 * m + kItemChunk - 1) / kItemChunk + 1;
+    HTD_CHECK(alloc_n(&w.items, w.items_cap));
+    if (h >= 3) {
+        w.bfs_list_len = n > 0 ? n : 1;
+        HTD_CHECK(alloc_n(&w.bfs_lists, (int64_t)w.grid_ball * 2 * w.bfs_list_len));
+    }
+    HTD_CHECK(cudaMalloc(&w.scan_tmp, scan_temp_bytes(n + 1)));
+    HTD_CHECK(alloc_n(&w.status, 1));
+    HTD_CHECK(cudaMallocHost(reinterpret_cast<void **>(&w.status_host), sizeof(DevStatus)));
+    return HTD_OK;
+}
+
+// Initial pass: every vertex's ball (count, reserve, store) and every edge's h-support,
+// then the first min reduction.  Leaves the status ready for round 0.
+htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
+                        htd_stats *timing) {
+    PeelWork &w = H->w;
+    GraphDev &g = H->g;
+    const int64_t n = g.n, m = g.m;
+    (void)h;
+    std::memset(w.status_host, 0, sizeof(DevStatus));
+    w.status_host->k = 2;
+    w.status_host->min_acc = INT_MAX;
+    HTD_CHECK(cudaMemcpyAsync(w.status, w.status_host, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
+    if (m > 0)
+        HTD_CHECK(cudaMemcpyAsync(w.col_live, g.col, 2 * m * sizeof(int32_t),
+                                  cudaMemcpyDeviceToDevice, s));
+    HTD_CHECK(cudaMemsetAsync(w.cand_stamp, 0xff, (n > 0 ? n : 1) * sizeof(int32_t), s));
+    HTD_CHECK(cudaMemsetAsync(w.changed_stamp, 0xff, (n > 0 ? n : 1) * sizeof(int32_t), s));
+    if (n > 0) {
+        k_init_deg<<<std::min<int64_t>((n + kBlock - 1) / kBlock, H->num_sms * 8), kBlock, 0, s>>>(
+            (int32_t)n, g.row_ptr, w.deg_alive);
+        (*launches)++;
+    }
+    BallArgs ba = ball_args(H);
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
+    if (timing) {
+        HTD_CHECK(cudaEventCreate(&e0));
+        HTD_CHECK(cudaEventCreate(&e1));
+        HTD_CHECK(cudaEventCreate(&e2));
+        HTD_CHECK(cudaEventCreate(&e3));
+    }
+    if (n > 0) {
+        k_ball<kModeCount><<<w.grid_ball, kBlock, w.smem_ball, s>>>(ba);
+        (*launches)++;
+        HTD_CHECK(cudaGetLastError());
+        HTD_CHECK(scan_exclusive<int32_t, int64_t>(w.ball_need, w.ball_off, n, w.scan_tmp, s, launches));
+        int64_t total = 0;
+        HTD_CHECK(cudaMemcpyAsync(&total, w.ball_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HTD_CHECK(cudaStreamSynchronize(s));
+        if (total > w.pool_words) {
+            cudaFree(w.pool);
+            w.pool = nullptr;
+            w.pool_words = 0;
+            HTD_CHECK(alloc_n(&w.pool, total));
+            w.pool_words = total;
+            if (H->graph_exec) {  // the captured rounds hold the old pool pointer
+                cudaGraphExecDestroy(H->graph_exec);
+                H->graph_exec = nullptr;
+            }
+        }
+        ba.pool = w.pool;
+        if (timing) HTD_CHECK(cudaEventRecord(e0, s));
+        k_ball<kModeStore><<<w.grid_ball, kBlock, w.smem_ball, s>>>(ba);
+        if (timing) HTD_CHECK(cudaEventRecord(e1, s));
+        (*launches)++;
+        HTD_CHECK(cudaGetLastError());
+        k_make_items<<<std::min<int64_t>((n + kBlock - 1) / kBlock, H->num_sms * 8), kBlock, 0, s>>>(
+            nullptr, 1, (int32_t)n, g.row_ptr, w.items, w.status);
+        (*launches)++;
+        HsupArgs ha = hsup_args(H, 1);
+        if (timing) HTD_CHECK(cudaEventRecord(e2, s));
+        k_hsup<<<w.grid_hsup, kBlock, w.smem_hsup, s>>>(ha);
+        if (timing) HTD_CHECK(cudaEventRecord(e3, s));
+        (*launches)++;
+        HTD_CHECK(cudaGetLastError());
+    }
+    k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 1);
+    (*launches)++;
+    HTD_CHECK(cudaGetLastError());
+    if (timing) {
+        HTD_CHECK(cudaStreamSynchronize(s));
+        float a = 0.f, b = 0.f;
+        if (n > 0) {
+            HTD_CHECK(cudaEventElapsedTime(&a, e0, e1));
+            HTD_CHECK(cudaEventElapsedTime(&b, e2, e3));
+            timing->ms_ball += a;
+            timing->ms_hsup += b;
+            timing->launches_ball += 1;
+            timing->launches_hsup += 1;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaEventDestroy(e2);
+        cudaEventDestroy(e3);
+    }
+    return HTD_OK;
+}
+
+// Enqueues one peel round.  evs (nullable) = 4 events: ball start/end, h-support start/end.
+htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t *evs) {
+    PeelWork &w = H->w;
+    GraphDev &g = H->g;
+    const int64_t m = g.m;
+    const int gsmall = H->num_sms * 4;
+    k_select<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, w.frontier);
+    k_cand_init<<<gsmall, kBlock, 0, s>>>(w.frontier, g.eu, g.ev, w.status, w.cand_stamp, w.cand_list);
+    *launches += 2;
+    for (int d = 1; d < w.h; d++) {
+        k_cand_expand<<<gsmall * 2, kBlock, 0, s>>>(d, g.row_ptr, w.col_live, w.status, w.cand_stamp,
+                                                     w.cand_list);
+        (*launches)++;
+    }
+    k_remove<<<gsmall, kBlock, 0, s>>>(w.frontier, w.status, g.eu, g.ev, g.slot_lo, g.slot_hi,
+                                       w.sup, w.truss, w.stamp, w.col_live, w.deg_alive);
+    (*launches)++;
+    BallArgs ba = ball_args(H);
+    if (evs) HTD_CHECK(cudaEventRecord(evs[0], s));
+    k_ball<kModeRebuild><<<w.grid_ball, kBlock, w.smem_ball, s>>>(ba);
+    if (evs) HTD_CHECK(cudaEventRecord(evs[1], s));
+    k_make_items<<<gsmall, kBlock, 0, s>>>(w.changed_list, 0, g.n, g.row_ptr, w.items, w.status);
+    HsupArgs ha = hsup_args(H, 0);
+    if (evs) HTD_CHECK(cudaEventRecord(evs[2], s));
+    k_hsup<<<w.grid_hsup, kBlock, w.smem_hsup, s>>>(ha);
+    if (evs) HTD_CHECK(cudaEventRecord(evs[3], s));
+    k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 0);
+    *launches += 4;
+    HTD_CHECK(cudaGetLastError());
+    return HTD_OK;
+}
+
+}  // namespace htd

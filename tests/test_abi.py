@@ -1,0 +1,82 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads, exports every
+symbol include/htruss.h declares, and the binding fails loudly instead of falling back."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "htruss.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2411_06405_gb300 import build, _lib
+
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(htd_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("htd_build_csr", "htd_h_support", "htd_truss_decompose"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2411_06405_gb300 import _lib
+
+    names = declared_functions()
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in htruss.h but not exported"
+    assert sorted(_lib.EXPORTED) == names
+
+
+def test_stats_struct_matches_header(lib):
+    from paper_2411_06405_gb300 import _lib
+
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct htd_stats \{(.*?)\} htd_stats;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(int64_t|int32_t|double|float)\s+(\w+);", body)
+    ctype = {"int64_t": ctypes.c_int64, "int32_t": ctypes.c_int32, "double": ctypes.c_double,
+             "float": ctypes.c_float}
+    assert [(n, ctype[t]) for t, n in fields] == list(_lib.HtdStats._fields_)
+
+
+def test_status_strings(lib):
+    for code in range(7):
+        assert lib.htd_status_string(code)
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    out = ctypes.c_void_p()
+    # NULL out pointer, negative n, n above the limit, oversized m_in: all host-side checks
+    assert lib.htd_build_csr(4, None, None, 0, 1, None, None) == 1
+    assert lib.htd_build_csr(-1, None, None, 0, 1, None, ctypes.byref(out)) == 1
+    assert lib.htd_build_csr(2_000_000, None, None, 0, 1, None, ctypes.byref(out)) == 6
+    assert lib.htd_build_csr(4, ctypes.c_void_p(8), ctypes.c_void_p(8), 1 << 30, 1, None,
+                             ctypes.byref(out)) == 5
+    assert not out.value
+    assert lib.htd_h_support(None, 2, None, None) == 1
+    assert lib.htd_truss_decompose(None, 2, None, None, None, None) == 1
+
+
+def test_no_cpu_fallback_without_a_gpu(lib):
+    import torch
+
+    import paper_2411_06405_gb300 as htd
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(Exception):
+        htd.htd_build_csr(3, torch.tensor([0, 1], dtype=torch.int32),
+                          torch.tensor([1, 2], dtype=torch.int32))

@@ -1,0 +1,282 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, bit-exact.
+
+Trussness and h-support are integers, so every comparison is exact equality.  Small and
+medium graphs are compared element by element; the full-size workloads are checked on
+sampled edges with the oracle's per-edge h-support and with the peeling certificate
+(stamp order on every edge, validity and removability on sampled edges), which together
+prove the whole output exact for the edges they cover.
+"""
+
+import numpy as np
+import pytest
+
+import pins
+from synth import barabasi_albert, config_graph, erdos_renyi_gnm, rmat, small_corpus
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def htd():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2411_06405_gb300 import build
+
+    build.build()
+    import paper_2411_06405_gb300 as mod
+
+    mod._lib.load()
+    torch.cuda.set_device(0)
+    return mod
+
+
+def gpu_graph(htd, n, s, d):
+    return htd.htd_build_csr(n, torch.from_numpy(np.asarray(s, dtype=np.int32)).cuda(),
+                             torch.from_numpy(np.asarray(d, dtype=np.int32)).cuda())
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+# ---- a1: normalisation, CSR and edge ids ----------------------------------------------------
+
+def csr_cases():
+    rng = np.random.default_rng(3)
+    cases = []
+    s, d = rmat(10, 16, 0.57, 0.19, 0.19, 31)  # loops + duplicates
+    cases.append(("rmat10_raw", 1 << 10, s, d))
+    # a hub above 4096 neighbours (shared-memory bit-set row sort), with duplicates
+    hub = np.zeros(9000, dtype=np.int32)
+    leaves = rng.integers(1, 6000, size=9000).astype(np.int32)
+    cases.append(("hub9000", 6000, np.concatenate([hub, leaves]), np.concatenate([leaves, hub])))
+    # rows of 33..4096 (block bitonic sort) and isolated vertices
+    s = rng.integers(0, 200, size=20000).astype(np.int32)
+    d = rng.integers(0, 200, size=20000).astype(np.int32)
+    cases.append(("dense200_isolated", 500, s, d))
+    cases.append(("empty_edges", 10, np.zeros(0, np.int32), np.zeros(0, np.int32)))
+    cases.append(("only_loops", 5, np.arange(5, dtype=np.int32), np.arange(5, dtype=np.int32)))
+    cases.append(("single_edge", 2, np.array([1], np.int32), np.array([0], np.int32)))
+    return cases
+
+
+@pytest.mark.parametrize("case", csr_cases(), ids=lambda c: c[0])
+def test_csr_and_edge_ids_match_oracle(htd, oracle_mod, case):
+    _, n, s, d = case
+    g = gpu_graph(htd, n, s, d)
+    eu_ref, ev_ref = oracle_mod.normalise(n, s, d)
+    assert g.m == eu_ref.size
+    eu, ev = htd.htd_edges(g)
+    np.testing.assert_array_equal(host(eu), eu_ref)
+    np.testing.assert_array_equal(host(ev), ev_ref)
+    row_ptr, col, slot_eid = (host(t) for t in htd.htd_csr(g))
+    deg = np.bincount(np.concatenate([eu_ref, ev_ref]), minlength=n)
+    np.testing.assert_array_equal(np.diff(row_ptr), deg)
+    for x in range(n):
+        r = col[row_ptr[x]:row_ptr[x + 1]]
+        assert (np.diff(r) > 0).all()
+    # slot -> edge id: the edge of slot (x, col) joins x and col
+    xs = np.repeat(np.arange(n), np.diff(row_ptr))
+    lo = np.minimum(xs, col)
+    hi = np.maximum(xs, col)
+    np.testing.assert_array_equal(eu_ref[slot_eid], lo)
+    np.testing.assert_array_equal(ev_ref[slot_eid], hi)
+
+
+def test_invalid_ids_rejected(htd):
+    with pytest.raises(htd.HtdError) as ei:
+        gpu_graph(htd, 4, [0, 1, 2], [1, 2, 4])
+    assert ei.value.status == 1
+    with pytest.raises(htd.HtdError):
+        gpu_graph(htd, 4, [0, -1], [1, 2])
+
+
+def test_invalid_h_rejected(htd):
+    g = gpu_graph(htd, 3, [0, 1], [1, 2])
+    for h in (0, 9, -1):
+        with pytest.raises(htd.HtdError):
+            htd.htd_h_support(g, h)
+        with pytest.raises(htd.HtdError):
+            htd.htd_truss_decompose(g, h)
+
+
+# ---- a2/a3: h-support -------------------------------------------------------------------------
+
+@pytest.mark.parametrize("h", [1, 2, 3, 4])
+def test_h_support_corpus(htd, oracle_mod, h):
+    for n, s, d in small_corpus(40, 100 + h, max_n=60):
+        g = gpu_graph(htd, n, s, d)
+        og = oracle_mod.OracleGraph.from_raw(n, s, d)
+        np.testing.assert_array_equal(host(htd.htd_h_support(g, h)), og.h_support(h))
+
+
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_h_support_er_n2000(htd, oracle_mod, h):
+    spec = config_graph("er_n2000")
+    g = gpu_graph(htd, spec.n, spec.src, spec.dst)
+    og = oracle_mod.OracleGraph.from_raw(spec.n, spec.src, spec.dst)
+    np.testing.assert_array_equal(host(htd.htd_h_support(g, h)), og.h_support(h))
+
+
+def test_h_support_against_floyd_warshall(htd):
+    # independent of the oracle: distances by Floyd-Warshall
+    for seed in range(10):
+        n = 30
+        s, d = erdos_renyi_gnm(n, 60, 900 + seed)
+        edges = pins.canonical(n, s, d)
+        g = gpu_graph(htd, n, s, d)
+        dist = pins.apsp(n, edges)
+        for h in (1, 2, 3, 5, 8):
+            np.testing.assert_array_equal(host(htd.htd_h_support(g, h)),
+                                          pins.sup_from_distances(dist, edges, h))
+
+
+# ---- a4-a7: peeling -----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("h", [1, 2, 3, 4])
+def test_truss_corpus(htd, oracle_mod, h):
+    for n, s, d in small_corpus(40, 200 + h, max_n=60):
+        g = gpu_graph(htd, n, s, d)
+        og = oracle_mod.OracleGraph.from_raw(n, s, d)
+        t, _, _ = htd.htd_truss_decompose(g, h)
+        np.testing.assert_array_equal(host(t), og.truss_decompose(h)[0])
+
+
+def test_truss_er_n2000_h2(htd, oracle_mod):
+    """The 2,000-vertex Erdos-Renyi workload at h=2, element by element."""
+    spec = config_graph("er_n2000")
+    g = gpu_graph(htd, spec.n, spec.src, spec.dst)
+    og = oracle_mod.OracleGraph.from_raw(spec.n, spec.src, spec.dst)
+    t_ref, _, _ = og.truss_decompose(2)
+    t, stamp, stats = htd.htd_truss_decompose(g, 2, stamps=True)
+    np.testing.assert_array_equal(host(t), t_ref)
+    assert stats["frontier_edges"] == g.m
+    assert stats["max_truss"] == t_ref.max()
+    order_bad, bad, _ = og.certify(2, host(t), host(stamp))
+    assert order_bad == 0 and bad.size == 0
+
+
+@pytest.mark.parametrize("h", [1, 3])
+def test_truss_er_other_h(htd, oracle_mod, h):
+    n, m = (2000, 8000) if h == 1 else (600, 2400)
+    s, d = erdos_renyi_gnm(n, m, 0x48545255)
+    g = gpu_graph(htd, n, s, d)
+    og = oracle_mod.OracleGraph.from_raw(n, s, d)
+    np.testing.assert_array_equal(host(htd.htd_truss_decompose(g, h)[0]),
+                                  og.truss_decompose(h)[0])
+
+
+def test_truss_ba_and_rmat(htd, oracle_mod):
+    for (n, (s, d)), h in (((400, barabasi_albert(400, 3, 41)), 2),
+                           ((512, rmat(9, 8, 0.57, 0.19, 0.19, 42)), 2),
+                           ((256, rmat(8, 8, 0.57, 0.19, 0.19, 43)), 3)):
+        g = gpu_graph(htd, n, s, d)
+        og = oracle_mod.OracleGraph.from_raw(n, s, d)
+        np.testing.assert_array_equal(host(htd.htd_truss_decompose(g, h)[0]),
+                                      og.truss_decompose(h)[0])
+
+
+@pytest.mark.parametrize("family,size", [("complete", 60), ("star", 5000), ("cycle", 1001),
+                                         ("path", 700), ("bipartite", (40, 70))])
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_closed_forms_large(htd, family, size, h):
+    build = {"complete": pins.complete, "star": pins.star, "path": pins.path,
+             "cycle": pins.cycle, "bipartite": lambda ab: pins.complete_bipartite(*ab)}[family]
+    edges = build(size)
+    n = 1 + max(max(e) for e in edges)
+    s = np.array([u for u, _ in edges], np.int32)
+    d = np.array([v for _, v in edges], np.int32)
+    g = gpu_graph(htd, n, s, d)
+    t, _, _ = htd.htd_truss_decompose(g, h)
+    assert set(host(t).tolist()) == {pins.closed_form_truss(family, size, h)}
+
+
+def test_disjoint_union_and_isolated(htd, oracle_mod):
+    parts = [(60, erdos_renyi_gnm(60, 200, 5)), (64, rmat(6, 6, 0.57, 0.19, 0.19, 6)),
+             (30, barabasi_albert(30, 3, 7))]
+    off = 0
+    ss, dd, ref = [], [], []
+    for n, (s, d) in parts:
+        og = oracle_mod.OracleGraph.from_raw(n, s, d)
+        ref.append(og.truss_decompose(2)[0])
+        ss.append(s + off)
+        dd.append(d + off)
+        off += n + 5  # five isolated vertices between components
+    g = gpu_graph(htd, off, np.concatenate(ss), np.concatenate(dd))
+    np.testing.assert_array_equal(host(htd.htd_truss_decompose(g, 2)[0]), np.concatenate(ref))
+
+
+def test_empty_graphs(htd):
+    for n, s, d in ((0, [], []), (7, [], []), (3, [1, 2], [1, 2])):
+        g = gpu_graph(htd, n, s, d)
+        assert g.m == 0
+        t, _, st = htd.htd_truss_decompose(g, 2)
+        assert t.numel() == 0 and st["rounds"] == 0
+        assert htd.htd_h_support(g, 3).numel() == 0
+
+
+def test_graph_and_direct_launch_agree_and_repeat(htd, oracle_mod):
+    s, d = rmat(11, 8, 0.57, 0.19, 0.19, 77)
+    g = gpu_graph(htd, 1 << 11, s, d)
+    t1, st1, s1 = htd.htd_truss_decompose(g, 2, stamps=True)
+    t2, st2, s2 = htd.htd_truss_decompose(g, 2, stamps=True, flags=htd.HTD_OPT_NO_GRAPH)
+    t3, _, s3 = htd.htd_truss_decompose(g, 2, flags=htd.HTD_OPT_TIMING)
+    assert torch.equal(t1, t2) and torch.equal(t1, t3)
+    assert s1["rounds"] == s2["rounds"] == s3["rounds"]
+    assert s3["launches_hsup"] >= 1
+    # changing h on the same handle and coming back
+    t_h3, _, _ = htd.htd_truss_decompose(g, 3)
+    t4, _, _ = htd.htd_truss_decompose(g, 2)
+    assert torch.equal(t1, t4)
+    assert (t_h3 >= t1).all()  # monotone in h
+    og = oracle_mod.OracleGraph.from_raw(1 << 11, s, d)
+    ob, bad, _ = og.certify(2, host(t1), host(st1))
+    assert ob == 0 and bad.size == 0
+
+
+def test_host_entry_point(htd, oracle_mod):
+    s, d = rmat(10, 8, 0.57, 0.19, 0.19, 88)
+    n = 1 << 10
+    eu, ev, t, stats = htd.htd_truss_decompose_host(n, s, d, 2)
+    og = oracle_mod.OracleGraph.from_raw(n, s, d)
+    np.testing.assert_array_equal(eu.numpy(), og.eu)
+    np.testing.assert_array_equal(ev.numpy(), og.ev)
+    np.testing.assert_array_equal(t.numpy(), og.truss_decompose(2)[0])
+
+
+# ---- full-size workloads (the benchmark's launch configuration) ---------------------------------
+
+def sample_edges(t, k, rng):
+    m = t.size
+    pick = set(rng.choice(m, size=min(k, m), replace=False).tolist())
+    order = np.argsort(t, kind="stable")
+    pick.update(order[:20].tolist())
+    pick.update(order[-20:].tolist())
+    return np.array(sorted(pick), dtype=np.int64)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,h", [("rmat_s18", 2), ("dcsbm_n200k", 2), ("dcsbm_n200k", 3)])
+def test_full_size_certificate(htd, oracle_mod, name, h):
+    spec = config_graph(name)
+    g = gpu_graph(htd, spec.n, spec.src, spec.dst)
+    og = oracle_mod.OracleGraph.from_raw(spec.n, spec.src, spec.dst)
+    eu, ev = htd.htd_edges(g)
+    np.testing.assert_array_equal(host(eu), og.eu)
+    np.testing.assert_array_equal(host(ev), og.ev)
+    sup = host(htd.htd_h_support(g, h))
+    t, stamp, stats = htd.htd_truss_decompose(g, h, stamps=True)
+    t, stamp = host(t), host(stamp)
+    assert stats["frontier_edges"] == g.m
+    assert (t >= 2).all() and (t <= sup + 2).all()
+    rng = np.random.default_rng(1234)
+    # h-support on sampled edges, one BFS pair each in the oracle
+    for e in rng.choice(g.m, size=60, replace=False):
+        assert sup[e] == og.edge_h_support(h, int(e))
+    # certificate: stamp order on all edges, validity + removability on sampled edges
+    edges = sample_edges(t, 80, rng)
+    order_bad, bad, codes = og.certify(h, t, stamp, edges)
+    assert order_bad == 0
+    assert bad.size == 0, f"certificate fails on edges {bad[:10]} codes {codes[:10]}"
