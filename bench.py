@@ -238,13 +238,27 @@ def run_gpu(args, world, rank, local):
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     s0 = stats[-1]
-    ms_ball = float(np.mean([s["ms_ball"] for s in stats]))
-    ms_hsup = float(np.mean([s["ms_hsup"] for s in stats]))
-    kern = "k_ball" if ms_ball >= ms_hsup else "k_hsup"
-    k_ms = ms_ball if kern == "k_ball" else ms_hsup
-    k_launches = s0["launches_ball"] if kern == "k_ball" else s0["launches_hsup"]
-    k_bytes = s0["alg_bytes_ball"] if kern == "k_ball" else s0["alg_bytes_hsup"]
-    achieved = (k_bytes / (k_ms / 1e3)) / 1e9 if k_ms > 0 else None
+
+    def mean(key):
+        return float(np.mean([s[key] for s in stats]))
+
+    rounds_timed = max(1, s0["timed_rounds"])
+    # kernel classes of one step: (name, device ms per step, launches per step, alg bytes)
+    ball_store_bytes = mean("alg_bytes_ball") / 2 if s0["incremental"] else None
+    classes = [
+        ("k_ball (initial store)", mean("ms_initial_ball"), 1, ball_store_bytes),
+        ("k_hsup (initial)", mean("ms_initial_hsup"), 1,
+         mean("alg_bytes_hsup") if s0["incremental"] else None),
+        ("k_loss_detect", mean("ms_find"), rounds_timed,
+         mean("alg_bytes_detect") if s0["incremental"] else None),
+        ("k_loss_delta + k_loss_apply", mean("ms_update"), 3 * rounds_timed,
+         mean("alg_bytes_update") if s0["incremental"] else None),
+    ]
+    if not s0["incremental"]:
+        classes = [("k_ball (rebuild rounds)", mean("ms_ball"), rounds_timed, None),
+                   ("k_hsup (rounds)", mean("ms_update"), rounds_timed, None)]
+    kern, k_ms, k_launches, k_bytes = max(classes, key=lambda c: c[1])
+    achieved = (k_bytes / (k_ms / 1e3)) / 1e9 if (k_bytes and k_ms > 0) else None
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
@@ -252,10 +266,14 @@ def run_gpu(args, world, rank, local):
             with open(prof) as f:
                 tj = json.load(f)
             ent = tj.get(args.workload, {}).get(kern)
-            if ent and k_launches:
+            if ent:
                 traffic = ent.get("bytes_per_launch")
         except (OSError, ValueError):
             traffic = None
+    phases = {name: {"ms": ms, "launches": ln, "alg_bytes": b} for name, ms, ln, b in classes}
+    phases["select"] = {"ms": mean("ms_select"), "launches": rounds_timed}
+    phases["remove"] = {"ms": mean("ms_remove"), "launches": rounds_timed}
+    phases["minreduce"] = {"ms": mean("ms_minreduce"), "launches": rounds_timed}
     hsup_rate = float(np.mean([s["hsup_evals"] for s in stats])) / (ms_step / 1e3)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -270,13 +288,14 @@ def run_gpu(args, world, rank, local):
                    "l2": "256 MiB buffer written between timed steps (untimed)"},
         "hsup_evals_per_sec": hsup_rate,
         "rounds": s0["rounds"], "levels": s0["levels"], "max_truss": s0["max_truss"],
-        "hsup_evals": s0["hsup_evals"], "ball_builds": s0["ball_builds"],
-        "ms_ball": ms_ball, "ms_hsup": ms_hsup,
+        "hsup_evals": s0["hsup_evals"], "pairs_tested": s0["pairs_tested"],
+        "pairs_lost": s0["pairs_lost"], "member_tests": s0["member_tests"],
+        "phases_ms_per_step": phases,
         "roofline": {"kernel": kern, "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
                      "traffic": traffic, "peak_source": peak_kind,
-                     "alg_bytes_per_launch": k_bytes / max(1, k_launches),
-                     "launches": k_launches},
+                     "alg_bytes_per_launch": (k_bytes / k_launches) if k_bytes else None,
+                     "launches_per_step": k_launches, "ms_per_launch": k_ms / k_launches},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(8 * k),
                 "d2h_bytes_per_step": int(12 * m), "ms_per_step": float(np.mean(e2e_ms))},
         "gpu_launches": int(launches // args.steps),

@@ -56,29 +56,47 @@ typedef enum htd_status {
 /* Opaque handle: the normalised graph in CSR form on one device plus cached scratch. */
 typedef struct htd_graph htd_graph;
 
-/* Counters of one decomposition (all zero for calls that do not peel). */
+/* Counters of one decomposition (all zero for calls that do not peel).  Times are device
+ * time between CUDA events on the library's stream, filled only with HTD_OPT_TIMING. */
 typedef struct htd_stats {
     int64_t rounds;          /* removal rounds (each removes every edge of the current level) */
     int64_t levels;          /* distinct k at which edges were removed */
     int32_t max_truss;       /* largest t(e,h) */
     int32_t h;
-    int64_t hsup_evals;      /* h-support evaluations: m (initial) + recomputations */
+    int64_t hsup_evals;      /* h-support evaluations: m (initial) + supports brought up to date
+                                in the rounds (edges with an endpoint whose ball shrank) */
     int64_t ball_builds;     /* h-hop balls built: n (initial) + rebuilt candidates */
     int64_t balls_changed;   /* rebuilt balls that had shrunk */
     int64_t frontier_edges;  /* edges removed (= m at the end) */
-    double alg_bytes_ball;   /* algorithmic bytes of the ball builds (see DESIGN notes) */
-    double alg_bytes_hsup;   /* algorithmic bytes of the h-support intersections */
-    float ms_ball;           /* device time in ball-build launches (timing option only) */
-    float ms_hsup;           /* device time in h-support launches (timing option only) */
-    int64_t launches_ball;   /* ball-build launches (timing option only) */
-    int64_t launches_hsup;   /* h-support launches (timing option only) */
+    int64_t pairs_tested;    /* incremental rounds: vertex pairs tested for loss */
+    int64_t pairs_lost;      /* incremental rounds: pairs that left each other's balls */
+    int64_t member_tests;    /* incremental rounds: ball-membership tests of support updates */
     int64_t kernel_launches; /* kernels this library launched for the call */
     int64_t ball_pool_bytes; /* device bytes held by the h-hop balls */
+    int64_t timed_rounds;    /* rounds whose phases were timed */
+    double alg_bytes_ball;   /* algorithmic bytes: ball builds (initial and rebuilds) */
+    double alg_bytes_hsup;   /* algorithmic bytes: full h-support intersections */
+    double alg_bytes_detect; /* algorithmic bytes: loss detection (incremental rounds) */
+    double alg_bytes_update; /* algorithmic bytes: support updates (incremental rounds) */
+    float ms_initial_ball;   /* initial pass: ball builds (count + store) */
+    float ms_initial_hsup;   /* initial pass: every edge's h-support */
+    float ms_select;         /* rounds: frontier selection */
+    float ms_find;           /* rounds: candidate search (rebuild) or loss detection */
+    float ms_remove;         /* rounds: edge removal */
+    float ms_ball;           /* rounds: ball rebuilds (rebuild variant) */
+    float ms_update;         /* rounds: support recomputation or incremental updates */
+    float ms_minreduce;      /* rounds: min alive support + alive count */
+    int32_t incremental;     /* 1 if the rounds used incremental support updates */
+    int32_t reserved;
 } htd_stats;
 
 /* Option flags for htd_truss_decompose_ex. */
 #define HTD_OPT_TIMING 1u    /* time ball-build and h-support launches with CUDA events */
 #define HTD_OPT_NO_GRAPH 2u  /* launch each peel round directly instead of via a CUDA graph */
+#define HTD_OPT_REBUILD 4u   /* h <= 2: rebuild shrunk balls and recompute their edges' support
+                                instead of the incremental lost-pair updates (same results) */
+#define HTD_OPT_TINY_LOSS_TABLE 8u  /* h <= 2: 128-slot lost-pair table, so that rounds run in
+                                       many batches (a test of that path; slow) */
 
 /* Normalise an undirected edge list and build the graph (Sec. 2 graph model).
  *   n            vertex count, ids in [0, n); 0 <= n <= HTD_MAX_N.

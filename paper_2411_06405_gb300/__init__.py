@@ -18,10 +18,12 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import HTD_MAX_H, HTD_MAX_N, HTD_OPT_NO_GRAPH, HTD_OPT_TIMING, HtdError, HtdStats
+from ._lib import (HTD_MAX_H, HTD_MAX_N, HTD_OPT_NO_GRAPH, HTD_OPT_REBUILD, HTD_OPT_TIMING,
+                   HTD_OPT_TINY_LOSS_TABLE, HtdError, HtdStats)
 
 __all__ = [
-    "HTD_MAX_H", "HTD_MAX_N", "HTD_OPT_NO_GRAPH", "HTD_OPT_TIMING", "HtdError", "HtdStats",
+    "HTD_MAX_H", "HTD_MAX_N", "HTD_OPT_NO_GRAPH", "HTD_OPT_REBUILD", "HTD_OPT_TIMING",
+    "HTD_OPT_TINY_LOSS_TABLE", "HtdError", "HtdStats",
     "Graph", "htd_build_csr", "htd_graph_info", "htd_edges", "htd_csr", "htd_h_support",
     "htd_truss_decompose", "htd_truss_decompose_host", "htd_graph_free", "library_path",
 ]

@@ -20,6 +20,8 @@ HTD_MAX_H = 8
 HTD_MAX_N = 1600000
 HTD_OPT_TIMING = 1
 HTD_OPT_NO_GRAPH = 2
+HTD_OPT_REBUILD = 4
+HTD_OPT_TINY_LOSS_TABLE = 8
 
 # every symbol include/htruss.h declares
 EXPORTED = (
@@ -39,14 +41,26 @@ class HtdStats(ctypes.Structure):
         ("ball_builds", ctypes.c_int64),
         ("balls_changed", ctypes.c_int64),
         ("frontier_edges", ctypes.c_int64),
-        ("alg_bytes_ball", ctypes.c_double),
-        ("alg_bytes_hsup", ctypes.c_double),
-        ("ms_ball", ctypes.c_float),
-        ("ms_hsup", ctypes.c_float),
-        ("launches_ball", ctypes.c_int64),
-        ("launches_hsup", ctypes.c_int64),
+        ("pairs_tested", ctypes.c_int64),
+        ("pairs_lost", ctypes.c_int64),
+        ("member_tests", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
         ("ball_pool_bytes", ctypes.c_int64),
+        ("timed_rounds", ctypes.c_int64),
+        ("alg_bytes_ball", ctypes.c_double),
+        ("alg_bytes_hsup", ctypes.c_double),
+        ("alg_bytes_detect", ctypes.c_double),
+        ("alg_bytes_update", ctypes.c_double),
+        ("ms_initial_ball", ctypes.c_float),
+        ("ms_initial_hsup", ctypes.c_float),
+        ("ms_select", ctypes.c_float),
+        ("ms_find", ctypes.c_float),
+        ("ms_remove", ctypes.c_float),
+        ("ms_ball", ctypes.c_float),
+        ("ms_update", ctypes.c_float),
+        ("ms_minreduce", ctypes.c_float),
+        ("incremental", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -76,9 +76,9 @@ htd_status check_status_err(const htd::DevStatus *st) {
     return HTD_OK;
 }
 
-htd_status prepare_work(Handle *H, int32_t h) {
-    if (H->w.status && H->w.h != h) destroy_graph(H);
-    return htd::ensure_work(H, h);
+htd_status prepare_work(Handle *H, int32_t h, bool incremental, bool tiny = false) {
+    if (H->w.status && (H->w.h != h || H->w.lost_tiny != tiny)) destroy_graph(H);
+    return htd::ensure_work(H, h, incremental, tiny);
 }
 
 }  // namespace
@@ -241,7 +241,7 @@ htd_status htd_h_support(htd_graph *g, int32_t h, int32_t *sup_dev, void *stream
     Handle *H = &g->H;
     cudaStream_t user = static_cast<cudaStream_t>(stream);
     API_TRY(begin_call(H, user));
-    API_TRY(prepare_work(H, h));
+    API_TRY(prepare_work(H, h, true));
     int64_t launches = 0;
     htd_status ip = htd::initial_pass(H, h, H->pstream, &launches, nullptr);
     htd::g_launches += launches;
@@ -278,7 +278,9 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
     };
 
     API_TRY(begin_call(H, user));
-    API_TRY(prepare_work(H, h));
+    bool incremental = (flags & HTD_OPT_REBUILD) == 0;
+    API_TRY(prepare_work(H, h, incremental, (flags & HTD_OPT_TINY_LOSS_TABLE) != 0));
+    incremental = w.incremental;
     {
         htd_status ip = htd::initial_pass(H, h, H->pstream, &launches, timing ? &local : nullptr);
         htd::g_launches += launches;
@@ -296,19 +298,20 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
         evs.clear();
     };
     if (timing) {
-        evs.resize(4 * R, nullptr);
+        evs.resize(htd::kRoundEvents * R, nullptr);
         for (auto &e : evs) API_CHECK(cudaEventCreate(&e));
     }
-    const int per_round = h + 6;
+    const int per_round = incremental ? 7 : h + 6;
     if (w.status_host->alive > 0) {
-        if (use_graph && (!H->graph_exec || H->graph_h != h || H->graph_rounds != (timing ? -R : R))) {
+        if (use_graph && (!H->graph_exec || H->graph_h != h || H->graph_rounds != (timing ? -R : R) ||
+                          H->graph_incremental != incremental)) {
             destroy_graph(H);
             cudaGraph_t graph = nullptr;
             API_CHECK(cudaStreamBeginCapture(H->pstream, cudaStreamCaptureModeThreadLocal));
             int64_t dummy = 0;
             htd_status cs = HTD_OK;
             for (int r = 0; r < R && cs == HTD_OK; r++)
-                cs = htd::enqueue_round(H, H->pstream, &dummy, timing ? &evs[4 * r] : nullptr);
+                cs = htd::enqueue_round(H, H->pstream, &dummy, timing ? &evs[htd::kRoundEvents * r] : nullptr);
             cudaError_t ce = cudaStreamEndCapture(H->pstream, &graph);
             if (cs != HTD_OK) {
                 if (graph) cudaGraphDestroy(graph);
@@ -330,11 +333,15 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
             }
             H->graph_h = h;
             H->graph_rounds = timing ? -R : R;
+            H->graph_incremental = incremental;
         }
         // timed graphs hold this call's events: recapture next time
         // every active round removes at least one edge, so m/R + 2 batches always suffice
         const int64_t round_cap = H->g.m + 2 * R + 2;
-        const int64_t batch_cap = H->g.m / R + 3;
+        // continued incremental rounds handle at least one new lost pair per slot, and a
+        // pair is lost at most once (sum of ball sizes / 2 pairs in all)
+        const int64_t batch_cap =
+            (H->g.m + (incremental ? w.status_host->st_ball_total / 2 + 1 : 0)) / R + 3;
         int64_t batches = 0;
         bool timing_ok = timing;
         while (w.status_host->alive > 0) {
@@ -349,8 +356,8 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
                 launches += (int64_t)R * per_round;
             } else {
                 for (int r = 0; r < R; r++) {
-                    htd_status rs = htd::enqueue_round(H, H->pstream, &launches,
-                                                       timing ? &evs[4 * r] : nullptr);
+                    htd_status rs = htd::enqueue_round(
+                        H, H->pstream, &launches, timing ? &evs[htd::kRoundEvents * r] : nullptr);
                     if (rs != HTD_OK) {
                         cleanup_events();
                         return rs;
@@ -368,21 +375,32 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
             }
             if (timing_ok) {
                 const int active = w.status_host->round - rounds_before;
-                for (int r = 0; r < active && r < R; r++) {
-                    float a = 0.f, b = 0.f;
-                    if (cudaEventElapsedTime(&a, evs[4 * r], evs[4 * r + 1]) != cudaSuccess ||
-                        cudaEventElapsedTime(&b, evs[4 * r + 2], evs[4 * r + 3]) != cudaSuccess) {
-                        (void)cudaGetLastError();  // not sticky: report "no timing" instead
-                        timing_ok = false;
-                        local.ms_ball = -1.f;
-                        local.ms_hsup = -1.f;
-                        break;
+                for (int r = 0; r < active && r < R && timing_ok; r++) {
+                    float t[htd::kRoundEvents - 1];
+                    for (int q = 0; q + 1 < htd::kRoundEvents; q++) {
+                        if (cudaEventElapsedTime(&t[q], evs[htd::kRoundEvents * r + q],
+                                                 evs[htd::kRoundEvents * r + q + 1]) != cudaSuccess) {
+                            (void)cudaGetLastError();  // not sticky: report "no timing" instead
+                            timing_ok = false;
+                            break;
+                        }
                     }
-                    local.ms_ball += a;
-                    local.ms_hsup += b;
-                    local.launches_ball += 1;
-                    local.launches_hsup += 1;
+                    if (!timing_ok) break;
+                    local.ms_select += t[0];
+                    if (incremental) {
+                        local.ms_remove += t[1];
+                        local.ms_find += t[2];
+                        local.ms_update += t[3] + t[4];
+                    } else {
+                        local.ms_find += t[1];
+                        local.ms_remove += t[2];
+                        local.ms_ball += t[3];
+                        local.ms_update += t[4];
+                    }
+                    local.ms_minreduce += t[5];
+                    local.timed_rounds += 1;
                 }
+                if (!timing_ok) local.timed_rounds = -1;
             }
             if (w.status_host->round > round_cap) {
                 cleanup_events();
@@ -406,11 +424,18 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
         local.levels = s->levels;
         local.max_truss = s->max_k;
         local.hsup_evals = m + s->st_recomputed;
+        local.pairs_tested = s->st_pairs;
+        local.pairs_lost = s->st_lost;
+        local.member_tests = s->st_tests;
+        local.incremental = incremental ? 1 : 0;
+        local.levels = s->levels;
         local.ball_builds = H->g.n + s->st_candidates;
         local.balls_changed = s->st_changed;
         local.frontier_edges = s->st_frontier;
         local.alg_bytes_ball = (double)s->st_bytes_ball;
         local.alg_bytes_hsup = (double)s->st_bytes_hsup;
+        local.alg_bytes_detect = (double)s->st_bytes_detect;
+        local.alg_bytes_update = (double)s->st_bytes_update;
         local.kernel_launches = launches;
         local.ball_pool_bytes = w.pool_words * 4;
         *stats = local;

@@ -38,6 +38,17 @@ struct DevStatus {
     int64_t st_recomputed;     // h-support recomputations (after the initial pass)
     unsigned long long st_bytes_ball;  // algorithmic bytes, ball builds
     unsigned long long st_bytes_hsup;  // algorithmic bytes, intersections
+    // incremental (h <= 2) rounds
+    int32_t nlost;             // lost-pair records of the current batch (duplicates nulled)
+    int32_t cont;              // 1: the current round continues (its frontier is removed)
+    int32_t unit_begin;        // first frontier edge side the next loss detection tests
+    int32_t overflow_unit;     // smallest edge side whose lost pairs did not fit (INT_MAX)
+    int64_t st_ball_total;     // sum of the initial ball sizes
+    int64_t st_pairs;          // candidate pairs tested
+    int64_t st_lost;           // lost pairs
+    int64_t st_tests;          // ball-membership tests of the support updates
+    unsigned long long st_bytes_detect;  // algorithmic bytes, loss detection
+    unsigned long long st_bytes_update;  // algorithmic bytes, incremental support updates
 };
 
 enum : int32_t {

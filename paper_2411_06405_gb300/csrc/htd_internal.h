@@ -6,7 +6,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/htruss.h"
+#include "htruss.h"
 #include "htd_common.cuh"
 
 namespace htd {
@@ -48,6 +48,13 @@ struct PeelWork {
     int32_t *changed_stamp = nullptr;  // n round in which the ball last shrank
     int2 *items = nullptr;         // (vertex, first slot) h-support work items
     int64_t items_cap = 0;
+    bool incremental = false;      // h <= 2: lost-pair support updates instead of rebuilds
+    unsigned long long *lost_keys = nullptr;  // hash set of the round's lost pairs
+    int64_t lost_cap = 0;          // hash slots (power of two)
+    int64_t lost_max = 0;          // lost-pair records one batch may hold (half the slots)
+    bool lost_tiny = false;        // table forced to 128 slots (test option)
+    int4 *lost = nullptr;          // (min, max, hash slot, 0) per lost pair
+    int32_t *edge_touch = nullptr; // m: last round whose support update touched the edge
     int32_t *bfs_lists = nullptr;  // per-block BFS level lists (h >= 3)
     int64_t bfs_list_len = 0;      // entries per list
     void *scan_tmp = nullptr;
@@ -68,7 +75,7 @@ struct Handle {
     cudaGraphExec_t graph_exec = nullptr; // cached round graph
     int graph_h = 0;
     int graph_rounds = 0;
-    int32_t *graph_truss = nullptr, *graph_stamp = nullptr;
+    bool graph_incremental = false;
     int num_sms = 0;
 };
 
@@ -80,10 +87,16 @@ htd_status build_csr_device(int32_t n, const int32_t *src, const int32_t *dst, i
 void free_graph_dev(GraphDev *g);
 
 // Ball builder, h-support and peel rounds (htd_peel.cu).
-htd_status ensure_work(Handle *H, int32_t h);
+htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table = false);
 void free_work(PeelWork *w);
 htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
                         htd_stats *timing);
+// evs (nullable): kRoundEvents events marking the phase boundaries of the round.
+constexpr int kRoundEvents = 7;
 htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t *evs);
+
+// Incremental support updates of one round, h <= 2 (htd_loss.cu).
+htd_status enqueue_loss_kernels(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t ev_mid,
+                                unsigned record_flags);
 
 }  // namespace htd

@@ -243,6 +243,8 @@ __global__ void __launch_bounds__(kBlock) k_ball(BallArgs a) {
                 }
             }
             if (threadIdx.x == 0 && stor <= cap) {
+                if (MODE == kModeStore) atomicAdd((unsigned long long *)&st->st_ball_total,
+                                                  (unsigned long long)size);
                 a.ball_size[x] = size;
                 a.ball_nw[x] = dense ? -1 : nzw;
                 if (MODE == kModeRebuild) {
@@ -414,7 +416,7 @@ __global__ void k_make_items(const int32_t *__restrict__ list, int32_t initial, 
 
 __global__ void k_select(const int32_t *__restrict__ sup, int64_t m, DevStatus *st,
                          int32_t *__restrict__ frontier) {
-    if (st->alive == 0) return;
+    if (st->alive == 0 || st->cont) return;  // a continued round keeps its frontier
     const int thr = st->k - 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); e0 < m; e0 += stride) {
@@ -477,7 +479,7 @@ __global__ void k_remove(const int32_t *__restrict__ frontier, DevStatus *st,
                          int32_t *__restrict__ sup, int32_t *__restrict__ truss,
                          int32_t *__restrict__ stamp, int32_t *__restrict__ col_live,
                          int32_t *__restrict__ deg_alive) {
-    if (st->alive == 0) return;
+    if (st->alive == 0 || st->cont) return;  // a continued round removed its frontier already
     const int nF = st->nF, k = st->k, round = st->round;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
         const int e = frontier[i];
@@ -496,38 +498,48 @@ __global__ void k_remove(const int32_t *__restrict__ frontier, DevStatus *st,
 // bookkeeping, next level k = max(k, min + 2) (Algorithm 1's bins skip empty levels),
 // and reset of the per-round counters.
 __global__ void __launch_bounds__(kBlock) k_minreduce(const int32_t *__restrict__ sup, int64_t m,
-                                                      DevStatus *st, int32_t initial) {
+                                                      DevStatus *st, int32_t initial,
+                                                      const int32_t *__restrict__ edge_touch) {
     __shared__ int32_t s_min[kNWarps];
     __shared__ long long s_cnt[kNWarps];
+    __shared__ long long s_touch[kNWarps];
     __shared__ bool s_last;
     if (!initial && st->alive == 0) return;
+    const int round = st->round;
+    // count touched edges once per round: in its last (finished) slot
+    const bool count_touch = edge_touch && st->overflow_unit == INT_MAX;
     int lmin = INT_MAX;
-    long long lc = 0;
+    long long lc = 0, lt = 0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int s = sup[e];
         if (s != INT_MAX) {
             lmin = min(lmin, s);
             lc++;
+            if (count_touch && edge_touch[e] == round) lt++;
         }
     }
     lmin = warp_min(lmin);
     lc = warp_sum_ll(lc);
+    lt = warp_sum_ll(lt);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
         s_min[wid] = lmin;
         s_cnt[wid] = lc;
+        s_touch[wid] = lt;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         int bm = INT_MAX;
-        long long bc = 0;
+        long long bc = 0, bt = 0;
         for (int j = 0; j < kNWarps; j++) {
             bm = min(bm, s_min[j]);
             bc += s_cnt[j];
+            bt += s_touch[j];
         }
         if (bm != INT_MAX) atomicMin(&st->min_acc, bm);
         if (bc) atomicAdd((unsigned long long *)&st->alive_acc, (unsigned long long)bc);
+        if (bt) atomicAdd((unsigned long long *)&st->st_recomputed, (unsigned long long)bt);
         __threadfence();
         const unsigned ticket = atomicAdd(&st->done_blocks, 1u);
         s_last = (ticket == gridDim.x - 1);
@@ -538,7 +550,12 @@ __global__ void __launch_bounds__(kBlock) k_minreduce(const int32_t *__restrict_
         const int mn = atomicAdd(&st->min_acc, 0);
         const long long al = (long long)atomicAdd((unsigned long long *)&st->alive_acc, 0ull);
         const int nF = st->nF;
-        if (!initial && nF > 0) {
+        // an incremental round whose lost pairs did not all fit continues in the next slot
+        const bool unfinished = !initial && st->overflow_unit != INT_MAX && al > 0;
+        st->cont = unfinished ? 1 : 0;
+        st->unit_begin = unfinished ? st->overflow_unit : 0;
+        st->overflow_unit = INT_MAX;
+        if (!initial && nF > 0 && !unfinished) {
             if (st->k != st->last_k) {
                 st->levels++;
                 st->last_k = st->k;
@@ -552,13 +569,14 @@ __global__ void __launch_bounds__(kBlock) k_minreduce(const int32_t *__restrict_
             st->st_changed += st->nchanged;
         }
         st->alive = al;
-        if (al > 0) st->k = max(st->k, mn + 2);
+        if (al > 0 && !unfinished) st->k = max(st->k, mn + 2);
         st->min_acc = INT_MAX;
         st->alive_acc = 0;
         st->done_blocks = 0u;
-        st->nF = 0;
+        if (!unfinished) st->nF = 0;
         for (int j = 0; j < kMaxH; j++) st->cand_cnt[j] = 0;
         st->nchanged = 0;
+        st->nlost = 0;
         st->nitems = 0;
         st->q_ball = 0;
         st->q_items = 0;
@@ -655,6 +673,9 @@ void free_work(PeelWork *w) {
     cudaFree(w->changed_stamp);
     cudaFree(w->items);
     cudaFree(w->bfs_lists);
+    cudaFree(w->lost_keys);
+    cudaFree(w->lost);
+    cudaFree(w->edge_touch);
     cudaFree(w->scan_tmp);
     cudaFree(w->status);
     if (w->status_host) cudaFreeHost(w->status_host);
@@ -662,10 +683,14 @@ void free_work(PeelWork *w) {
 }
 
 // Allocates (or reuses) the scratch of an h-support pass / peel at hop threshold h.
-htd_status ensure_work(Handle *H, int32_t h) {
+htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) {
     PeelWork &w = H->w;
     GraphDev &g = H->g;
-    if (w.status && w.h == h) return HTD_OK;
+    incremental = incremental && h <= 2;
+    if (w.status && w.h == h && (!incremental || (w.lost_keys && w.lost_tiny == tiny_table))) {
+        w.incremental = incremental;
+        return HTD_OK;
+    }
     if (w.status) {
         // the per-block BFS lists and the ball storage depend on h: rebuild everything
         free_work(&w);
@@ -717,6 +742,19 @@ htd_status ensure_work(Handle *H, int32_t h) {
         w.bfs_list_len = n > 0 ? n : 1;
         HTD_CHECK(alloc_n(&w.bfs_lists, (int64_t)w.grid_ball * 2 * w.bfs_list_len));
     }
+    if (incremental) {
+        // a round's lost pairs: half of a power-of-two table of 8 x (2m) slots (>= 2^12)
+        int64_t cap = 4096;
+        while (cap < 16 * m && cap < ((int64_t)1 << 28)) cap <<= 1;
+        if (tiny_table) cap = 128;  // forces rounds to run in many batches
+        w.lost_tiny = tiny_table;
+        w.lost_cap = cap;
+        w.lost_max = cap / 2;
+        HTD_CHECK(alloc_n(&w.lost_keys, cap));
+        HTD_CHECK(alloc_n(&w.lost, w.lost_max));
+        HTD_CHECK(alloc_n(&w.edge_touch, m));
+    }
+    w.incremental = incremental;
     HTD_CHECK(cudaMalloc(&w.scan_tmp, scan_temp_bytes(n + 1)));
     HTD_CHECK(alloc_n(&w.status, 1));
     HTD_CHECK(cudaMallocHost(reinterpret_cast<void **>(&w.status_host), sizeof(DevStatus)));
@@ -734,12 +772,18 @@ htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
     std::memset(w.status_host, 0, sizeof(DevStatus));
     w.status_host->k = 2;
     w.status_host->min_acc = INT_MAX;
+    w.status_host->overflow_unit = INT_MAX;
     HTD_CHECK(cudaMemcpyAsync(w.status, w.status_host, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
     if (m > 0)
         HTD_CHECK(cudaMemcpyAsync(w.col_live, g.col, 2 * m * sizeof(int32_t),
                                   cudaMemcpyDeviceToDevice, s));
     HTD_CHECK(cudaMemsetAsync(w.cand_stamp, 0xff, (n > 0 ? n : 1) * sizeof(int32_t), s));
     HTD_CHECK(cudaMemsetAsync(w.changed_stamp, 0xff, (n > 0 ? n : 1) * sizeof(int32_t), s));
+    HTD_CHECK(cudaMemsetAsync(w.stamp, 0xff, (m > 0 ? m : 1) * sizeof(int32_t), s));
+    if (w.incremental) {
+        HTD_CHECK(cudaMemsetAsync(w.edge_touch, 0xff, (m > 0 ? m : 1) * sizeof(int32_t), s));
+        HTD_CHECK(cudaMemsetAsync(w.lost_keys, 0xff, w.lost_cap * sizeof(unsigned long long), s));
+    }
     if (n > 0) {
         k_init_deg<<<std::min<int64_t>((n + kBlock - 1) / kBlock, H->num_sms * 8), kBlock, 0, s>>>(
             (int32_t)n, g.row_ptr, w.deg_alive);
@@ -788,7 +832,7 @@ htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
         (*launches)++;
         HTD_CHECK(cudaGetLastError());
     }
-    k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 1);
+    k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 1, nullptr);
     (*launches)++;
     HTD_CHECK(cudaGetLastError());
     if (timing) {
@@ -797,10 +841,8 @@ htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
         if (n > 0) {
             HTD_CHECK(cudaEventElapsedTime(&a, e0, e1));
             HTD_CHECK(cudaEventElapsedTime(&b, e2, e3));
-            timing->ms_ball += a;
-            timing->ms_hsup += b;
-            timing->launches_ball += 1;
-            timing->launches_hsup += 1;
+            timing->ms_initial_ball += a;
+            timing->ms_initial_hsup += b;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -810,13 +852,40 @@ htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
     return HTD_OK;
 }
 
-// Enqueues one peel round.  evs (nullable) = 4 events: ball start/end, h-support start/end.
+// Enqueues one peel round.  evs (nullable) = kRoundEvents events at the phase boundaries:
+//   rebuild:     | select | candidates | remove | ball rebuild | items + h-support | reduce |
+//   incremental: | select | remove | loss detection | support updates | (empty) | reduce |
 htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t *evs) {
     PeelWork &w = H->w;
     GraphDev &g = H->g;
     const int64_t m = g.m;
     const int gsmall = H->num_sms * 4;
+    // inside a stream capture an ordinary record only orders nodes; an external record
+    // node really records the event each time the graph runs, so it can be timed
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (evs) HTD_CHECK(cudaStreamIsCapturing(s, &cap));
+    const unsigned rec_flags = (cap == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : 0u;
+    auto mark = [&](int i) {
+        if (evs) cudaEventRecordWithFlags(evs[i], s, rec_flags);
+    };
+    mark(0);
     k_select<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, w.frontier);
+    mark(1);
+    if (w.incremental) {
+        k_remove<<<gsmall, kBlock, 0, s>>>(w.frontier, w.status, g.eu, g.ev, g.slot_lo, g.slot_hi,
+                                           w.sup, w.truss, w.stamp, w.col_live, w.deg_alive);
+        mark(2);
+        *launches += 2;
+        htd_status ls = enqueue_loss_kernels(H, s, launches, evs ? evs[3] : nullptr, rec_flags);
+        if (ls != HTD_OK) return ls;
+        mark(4);
+        mark(5);
+        k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 0, w.edge_touch);
+        mark(6);
+        (*launches)++;
+        HTD_CHECK(cudaGetLastError());
+        return HTD_OK;
+    }
     k_cand_init<<<gsmall, kBlock, 0, s>>>(w.frontier, g.eu, g.ev, w.status, w.cand_stamp, w.cand_list);
     *launches += 2;
     for (int d = 1; d < w.h; d++) {
@@ -824,19 +893,20 @@ htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent
                                                      w.cand_list);
         (*launches)++;
     }
+    mark(2);
     k_remove<<<gsmall, kBlock, 0, s>>>(w.frontier, w.status, g.eu, g.ev, g.slot_lo, g.slot_hi,
                                        w.sup, w.truss, w.stamp, w.col_live, w.deg_alive);
     (*launches)++;
+    mark(3);
     BallArgs ba = ball_args(H);
-    if (evs) HTD_CHECK(cudaEventRecord(evs[0], s));
     k_ball<kModeRebuild><<<w.grid_ball, kBlock, w.smem_ball, s>>>(ba);
-    if (evs) HTD_CHECK(cudaEventRecord(evs[1], s));
+    mark(4);
     k_make_items<<<gsmall, kBlock, 0, s>>>(w.changed_list, 0, g.n, g.row_ptr, w.items, w.status);
     HsupArgs ha = hsup_args(H, 0);
-    if (evs) HTD_CHECK(cudaEventRecord(evs[2], s));
     k_hsup<<<w.grid_hsup, kBlock, w.smem_hsup, s>>>(ha);
-    if (evs) HTD_CHECK(cudaEventRecord(evs[3], s));
-    k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 0);
+    mark(5);
+    k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 0, nullptr);
+    mark(6);
     *launches += 4;
     HTD_CHECK(cudaGetLastError());
     return HTD_OK;

@@ -135,22 +135,29 @@ def test_h_support_against_floyd_warshall(htd):
 
 # ---- a4-a7: peeling -----------------------------------------------------------------------------
 
+MODES = {"incremental": 0, "rebuild": 4}
+
+
+@pytest.mark.parametrize("mode", sorted(MODES))
 @pytest.mark.parametrize("h", [1, 2, 3, 4])
-def test_truss_corpus(htd, oracle_mod, h):
+def test_truss_corpus(htd, oracle_mod, h, mode):
     for n, s, d in small_corpus(40, 200 + h, max_n=60):
         g = gpu_graph(htd, n, s, d)
         og = oracle_mod.OracleGraph.from_raw(n, s, d)
-        t, _, _ = htd.htd_truss_decompose(g, h)
+        t, _, st = htd.htd_truss_decompose(g, h, flags=MODES[mode])
         np.testing.assert_array_equal(host(t), og.truss_decompose(h)[0])
+        if g.m:
+            assert st["incremental"] == (1 if (h <= 2 and mode == "incremental") else 0)
 
 
-def test_truss_er_n2000_h2(htd, oracle_mod):
+@pytest.mark.parametrize("mode", sorted(MODES))
+def test_truss_er_n2000_h2(htd, oracle_mod, mode):
     """The 2,000-vertex Erdos-Renyi workload at h=2, element by element."""
     spec = config_graph("er_n2000")
     g = gpu_graph(htd, spec.n, spec.src, spec.dst)
     og = oracle_mod.OracleGraph.from_raw(spec.n, spec.src, spec.dst)
     t_ref, _, _ = og.truss_decompose(2)
-    t, stamp, stats = htd.htd_truss_decompose(g, 2, stamps=True)
+    t, stamp, stats = htd.htd_truss_decompose(g, 2, stamps=True, flags=MODES[mode])
     np.testing.assert_array_equal(host(t), t_ref)
     assert stats["frontier_edges"] == g.m
     assert stats["max_truss"] == t_ref.max()
@@ -158,24 +165,27 @@ def test_truss_er_n2000_h2(htd, oracle_mod):
     assert order_bad == 0 and bad.size == 0
 
 
+@pytest.mark.parametrize("mode", sorted(MODES))
 @pytest.mark.parametrize("h", [1, 3])
-def test_truss_er_other_h(htd, oracle_mod, h):
+def test_truss_er_other_h(htd, oracle_mod, h, mode):
     n, m = (2000, 8000) if h == 1 else (600, 2400)
     s, d = erdos_renyi_gnm(n, m, 0x48545255)
     g = gpu_graph(htd, n, s, d)
     og = oracle_mod.OracleGraph.from_raw(n, s, d)
-    np.testing.assert_array_equal(host(htd.htd_truss_decompose(g, h)[0]),
+    np.testing.assert_array_equal(host(htd.htd_truss_decompose(g, h, flags=MODES[mode])[0]),
                                   og.truss_decompose(h)[0])
 
 
-def test_truss_ba_and_rmat(htd, oracle_mod):
+@pytest.mark.parametrize("mode", sorted(MODES))
+def test_truss_ba_and_rmat(htd, oracle_mod, mode):
     for (n, (s, d)), h in (((400, barabasi_albert(400, 3, 41)), 2),
                            ((512, rmat(9, 8, 0.57, 0.19, 0.19, 42)), 2),
+                           ((1024, rmat(10, 8, 0.57, 0.19, 0.19, 44)), 1),
                            ((256, rmat(8, 8, 0.57, 0.19, 0.19, 43)), 3)):
         g = gpu_graph(htd, n, s, d)
         og = oracle_mod.OracleGraph.from_raw(n, s, d)
-        np.testing.assert_array_equal(host(htd.htd_truss_decompose(g, h)[0]),
-                                      og.truss_decompose(h)[0])
+        np.testing.assert_array_equal(
+            host(htd.htd_truss_decompose(g, h, flags=MODES[mode])[0]), og.truss_decompose(h)[0])
 
 
 @pytest.mark.parametrize("family,size", [("complete", 60), ("star", 5000), ("cycle", 1001),
@@ -223,9 +233,14 @@ def test_graph_and_direct_launch_agree_and_repeat(htd, oracle_mod):
     t1, st1, s1 = htd.htd_truss_decompose(g, 2, stamps=True)
     t2, st2, s2 = htd.htd_truss_decompose(g, 2, stamps=True, flags=htd.HTD_OPT_NO_GRAPH)
     t3, _, s3 = htd.htd_truss_decompose(g, 2, flags=htd.HTD_OPT_TIMING)
-    assert torch.equal(t1, t2) and torch.equal(t1, t3)
-    assert s1["rounds"] == s2["rounds"] == s3["rounds"]
-    assert s3["launches_hsup"] >= 1
+    t5, st5, s5 = htd.htd_truss_decompose(g, 2, stamps=True,
+                                          flags=htd.HTD_OPT_REBUILD | htd.HTD_OPT_TIMING)
+    assert torch.equal(t1, t2) and torch.equal(t1, t3) and torch.equal(t1, t5)
+    assert torch.equal(st1, st5)  # same level-synchronous schedule
+    assert s1["rounds"] == s2["rounds"] == s3["rounds"] == s5["rounds"]
+    assert s3["timed_rounds"] == s3["rounds"] and s3["ms_find"] > 0
+    assert s5["timed_rounds"] == s5["rounds"] and s5["ms_ball"] > 0
+    assert s1["incremental"] == 1 and s5["incremental"] == 0
     # changing h on the same handle and coming back
     t_h3, _, _ = htd.htd_truss_decompose(g, 3)
     t4, _, _ = htd.htd_truss_decompose(g, 2)
@@ -255,6 +270,32 @@ def sample_edges(t, k, rng):
     pick.update(order[:20].tolist())
     pick.update(order[-20:].tolist())
     return np.array(sorted(pick), dtype=np.int64)
+
+
+def test_incremental_matches_rebuild_on_hubby_graph(htd):
+    # R-MAT scale 13: hubs, thousands of rounds; both round variants must agree exactly
+    s, d = rmat(13, 8, 0.57, 0.19, 0.19, 99)
+    g = gpu_graph(htd, 1 << 13, s, d)
+    for h in (1, 2):
+        a, sa, st_a = htd.htd_truss_decompose(g, h, stamps=True)
+        b, sb, st_b = htd.htd_truss_decompose(g, h, stamps=True, flags=htd.HTD_OPT_REBUILD)
+        assert st_a["incremental"] == 1 and st_b["incremental"] == 0
+        assert torch.equal(a, b) and torch.equal(sa, sb)
+
+
+@pytest.mark.parametrize("h", [1, 2])
+def test_batched_rounds_match_oracle(htd, oracle_mod, h):
+    # a 128-slot lost-pair table splits most rounds into many batches
+    for (n, (s, d)) in ((512, rmat(9, 8, 0.57, 0.19, 0.19, 61)),
+                        (300, erdos_renyi_gnm(300, 1500, 62))):
+        g = gpu_graph(htd, n, s, d)
+        og = oracle_mod.OracleGraph.from_raw(n, s, d)
+        t, stamp, st = htd.htd_truss_decompose(g, h, stamps=True,
+                                               flags=htd.HTD_OPT_TINY_LOSS_TABLE)
+        t_ref, stamp_ref, rounds = og.truss_decompose(h)
+        np.testing.assert_array_equal(host(t), t_ref)
+        np.testing.assert_array_equal(host(stamp), stamp_ref)  # same rounds as the oracle
+        assert st["rounds"] == rounds and st["incremental"] == 1
 
 
 @pytest.mark.slow
