@@ -301,7 +301,7 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
         evs.resize(htd::kRoundEvents * R, nullptr);
         for (auto &e : evs) API_CHECK(cudaEventCreate(&e));
     }
-    const int per_round = incremental ? 7 : h + 6;
+    const int per_round = incremental ? 9 : h + 6;
     if (w.status_host->alive > 0) {
         if (use_graph && (!H->graph_exec || H->graph_h != h || H->graph_rounds != (timing ? -R : R) ||
                           H->graph_incremental != incremental)) {

@@ -43,6 +43,10 @@ struct DevStatus {
     int32_t cont;              // 1: the current round continues (its frontier is removed)
     int32_t unit_begin;        // first frontier edge side the next loss detection tests
     int32_t overflow_unit;     // smallest edge side whose lost pairs did not fit (INT_MAX)
+    int32_t npitems;           // loss detection items of the current batch
+    int32_t nuitems;           // support update items of the current batch
+    int32_t pad1;
+    long long upd_work;        // adjacency slots reserved for the batch's updates
     int64_t st_ball_total;     // sum of the initial ball sizes
     int64_t st_pairs;          // candidate pairs tested
     int64_t st_lost;           // lost pairs

@@ -36,6 +36,7 @@ struct PeelWork {
     int32_t *ball_need = nullptr;  // n storage words of the initial balls
     int32_t *ball_size = nullptr;  // n members of each ball (the vertex itself included)
     int32_t *ball_nw = nullptr;    // n: -1 = dense (W words), else (index,bits) pair count
+    int2 *ball_meta = nullptr;     // n: (offset / 4, ball_nw) packed for one-load lookups
     int32_t *col_live = nullptr;   // 2m neighbour ids, ~id once the edge is removed
     int32_t *deg_alive = nullptr;  // n alive degrees
     int32_t *sup = nullptr;        // m h-support (INT_MAX once removed)
@@ -54,7 +55,17 @@ struct PeelWork {
     int64_t lost_max = 0;          // lost-pair records one batch may hold (half the slots)
     bool lost_tiny = false;        // table forced to 128 slots (test option)
     int4 *lost = nullptr;          // (min, max, hash slot, 0) per lost pair
-    int32_t *edge_touch = nullptr; // m: last round whose support update touched the edge
+    int32_t *edge_touch = nullptr; // n: last round in which the vertex's ball lost a member
+    int32_t *hub_slot = nullptr;   // n: row of the vertex's alive-adjacency set, or -1
+    int32_t *hub_list = nullptr;   // nhub vertices with such a set (degree >= hub_min_deg)
+    uint32_t *hub_bits = nullptr;  // nhub x Wpad words: alive neighbours as n-bit sets
+    int32_t nhub = 0;
+    int32_t hub_min_deg = 0;
+    int2 *pitems = nullptr;        // loss detection items: (edge side, first slot), <= 32 pairs
+    int64_t pitems_cap = 0;
+    int2 *uitems = nullptr;        // support update items: (directed loss, first slot), <= 32
+    int64_t uitems_cap = 0;
+    int64_t upd_budget = 0;        // adjacency slots one batch of updates may visit
     int32_t *bfs_lists = nullptr;  // per-block BFS level lists (h >= 3)
     int64_t bfs_list_len = 0;      // entries per list
     void *scan_tmp = nullptr;

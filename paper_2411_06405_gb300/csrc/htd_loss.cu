@@ -47,11 +47,21 @@ struct LossArgs {
     uint32_t *pool;
     const int64_t *ball_off;
     const int32_t *ball_nw;
+    const int2 *ball_meta;
     int32_t *ball_size;
     unsigned long long *keys;
     int4 *lost;
     int32_t *sup;
-    int32_t *edge_touch;
+    int32_t *vtouch;
+    const int32_t *deg_alive;
+    const int32_t *hub_slot;
+    const uint32_t *hub_bits;
+    int32_t Wpad;
+    int32_t pitems_cap;
+    int2 *pitems;
+    int32_t uitems_cap;
+    int2 *uitems;
+    long long upd_budget;
     DevStatus *st;
 };
 
@@ -70,9 +80,22 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
     return k;
 }
 
-// Is q an alive neighbour of p?  Binary search in p's sorted row, then the alive mark.
-// `reads` counts the 4-byte words the search touches (algorithmic bytes = 4 x reads).
-__device__ __forceinline__ bool alive_adjacent(const LossArgs &a, int p, int q, unsigned &reads) {
+// Alive-adjacency set of p if p has one (high degree), else null.
+__device__ __forceinline__ const uint32_t *hub_set(const LossArgs &a, int p, unsigned &reads) {
+    reads++;
+    const int hs = a.hub_slot[p];
+    return hs >= 0 ? a.hub_bits + (int64_t)hs * a.Wpad : nullptr;
+}
+
+// Is q an alive neighbour of p?  One bit of p's alive-adjacency set when p has one, else a
+// binary search in p's sorted row and the alive mark.  `reads` counts the 4-byte words
+// touched (algorithmic bytes = 4 x reads).
+__device__ __forceinline__ bool alive_adjacent_set(const LossArgs &a, const uint32_t *pset, int p,
+                                                   int q, unsigned &reads) {
+    if (pset) {
+        reads++;
+        return (pset[q >> 5] >> (q & 31)) & 1u;
+    }
     int lo = a.row_ptr[p], hi = a.row_ptr[p + 1] - 1;
     reads += 2;
     while (lo <= hi) {
@@ -89,8 +112,19 @@ __device__ __forceinline__ bool alive_adjacent(const LossArgs &a, int p, int q, 
     return false;
 }
 
-// dist(p,q) <= h in the alive graph, p != q, h in {1,2}.
-__device__ bool within_h(const LossArgs &a, int p, int q, unsigned &reads) {
+__device__ __forceinline__ bool alive_adjacent(const LossArgs &a, int p, int q, unsigned &reads) {
+    return alive_adjacent_set(a, hub_set(a, p, reads), p, q, reads);
+}
+
+// Short rows are scanned by one lane; pairs whose shorter row is longer go to the warp.
+constexpr int kInlineScan = 4;
+
+enum PairState { kKept = 0, kLost = 1, kHard = 2 };
+
+// First test of the pair {p,q} (p != q) in the alive graph, by one lane: adjacency by
+// binary search in the shorter row, then (h = 2) a common alive neighbour when the shorter
+// row is at most kInlineScan long.  Longer scans are left to the warp (kHard).
+__device__ __forceinline__ int pair_quick(const LossArgs &a, int &p, int &q, unsigned &reads) {
     const int dp = a.row_ptr[p + 1] - a.row_ptr[p];
     const int dq = a.row_ptr[q + 1] - a.row_ptr[q];
     reads += 4;
@@ -99,25 +133,48 @@ __device__ bool within_h(const LossArgs &a, int p, int q, unsigned &reads) {
         p = q;
         q = t;
     }
-    if (alive_adjacent(a, p, q, reads)) return true;
-    if (a.h < 2) return false;
+    const uint32_t *qset = hub_set(a, q, reads);
+    if (alive_adjacent_set(a, qset, q, p, reads)) return kKept;
+    if (a.h < 2) return kLost;
+    // with q's set every scanned neighbour costs one read; without it, a binary search
+    if (min(dp, dq) > (qset ? 8 * kInlineScan : kInlineScan)) return kHard;
     const int re = a.row_ptr[p + 1];
     for (int s = a.row_ptr[p]; s < re; s++) {
         const int y = a.col_live[s];
         reads++;
-        if (y >= 0 && alive_adjacent(a, q, y, reads)) return true;
+        if (y >= 0 && alive_adjacent_set(a, qset, q, y, reads)) return kKept;
+    }
+    return kLost;
+}
+
+// Common alive neighbour of p (shorter row) and q, searched by the whole warp: lanes take
+// p's slots 32 at a time and binary-search them in q's row; stops at the first hit.
+__device__ __forceinline__ bool warp_common_neighbour(const LossArgs &a, int p, int q,
+                                                      unsigned &reads) {
+    const int lane = threadIdx.x & 31;
+    const int rb = a.row_ptr[p], re = a.row_ptr[p + 1];
+    const uint32_t *qset = hub_set(a, q, reads);
+    for (int s0 = rb; s0 < re; s0 += 32) {
+        const int s = s0 + lane;
+        bool hit = false;
+        if (s < re) {
+            const int y = a.col_live[s];
+            reads++;
+            hit = (y >= 0) && alive_adjacent_set(a, qset, q, y, reads);
+        }
+        if (__any_sync(0xffffffffu, hit)) return true;
     }
     return false;
 }
 
 // Is w in the stored ball of z (dense words, or sorted (word index, word) pairs)?
-// `bytes` counts the algorithmic bytes: 12 of metadata plus the words probed.
-__device__ __forceinline__ bool ball_contains(const LossArgs &a, int z, int w, unsigned &bytes) {
-    const int nw = a.ball_nw[z];
-    const int64_t off = a.ball_off[z];
+// `bytes` counts the algorithmic bytes: 8 of metadata plus the words probed.
+__device__ __forceinline__ bool ball_contains_meta(const LossArgs &a, int2 meta, int w,
+                                                   unsigned &bytes) {
+    const int nw = meta.y;
+    const int64_t off = (int64_t)(unsigned)meta.x << 2;
     const uint32_t bit = 1u << (w & 31);
     const uint32_t wi = (uint32_t)(w >> 5);
-    bytes += 12;
     if (nw < 0) {
         bytes += 4;
         return (a.pool[off + wi] & bit) != 0u;
@@ -135,9 +192,100 @@ __device__ __forceinline__ bool ball_contains(const LossArgs &a, int z, int w, u
     return false;
 }
 
-// Enumerates and tests the candidate pairs of every frontier edge (one warp per edge side):
-// side 0 of (a,b) pairs a with {b} ∪ N_old(b) \ {a}; side 1 pairs b with N_old(a) \ {b}.
-// "Old" adjacency = slots alive before this round: alive now, or removed in this round.
+__device__ __forceinline__ bool ball_contains(const LossArgs &a, int z, int w, unsigned &bytes) {
+    bytes += 8;
+    return ball_contains_meta(a, a.ball_meta[z], w, bytes);
+}
+
+// Records the lost pair {x,z} unless an earlier batch of this round handled it.  The
+// record and the pair's update work (both rows are visited by the support updates) are
+// reserved against the batch limits; a pair that does not fit marks its edge side u as
+// the point where the next slot of this round resumes.
+__device__ __forceinline__ void record_lost(const LossArgs &a, DevStatus *st, int x, int z, int u,
+                                            unsigned &reads) {
+    if (!ball_contains(a, x, z, reads)) return;  // stored bit already clear
+    const long long work = (long long)(a.row_ptr[x + 1] - a.row_ptr[x]) +
+                           (a.row_ptr[z + 1] - a.row_ptr[z]);
+    const long long before =
+        (long long)atomicAdd((unsigned long long *)&st->upd_work, (unsigned long long)work);
+    const int idx = atomicAdd(&st->nlost, 1);
+    if (idx >= a.lost_max || before + work > a.upd_budget) {
+        atomicMin(&st->overflow_unit, u);
+        if (idx < a.lost_max) a.lost[idx] = make_int4(-1, -1, -1, 0);
+        return;
+    }
+    const unsigned long long key = pair_key(x, z);
+    unsigned long long slot = mix64(key) & a.cap_mask;
+    int4 rec = make_int4(-1, -1, -1, 0);  // null record: the pair is already held
+    for (unsigned long long probe = 0; probe <= a.cap_mask; probe++) {
+        const unsigned long long prev = atomicCAS(a.keys + slot, kEmpty, key);
+        if (prev == kEmpty) {
+            rec = make_int4(min(x, z), max(x, z), (int)slot, 0);
+            break;
+        }
+        if (prev == key) break;
+        slot = (slot + 1) & a.cap_mask;
+    }
+    a.lost[idx] = rec;
+}
+
+// Pair enumeration of edge side u = (edge F[u/2], side u%2): side 0 of (a,b) pairs a with
+// {b} and with N_old(b) \ {a} (slots start-1 .. re-1 of b's row, start-1 standing for b);
+// side 1 pairs b with N_old(a) \ {b}.  For h = 1 only {a,b}.
+struct UnitInfo {
+    int x, y, rb, start, stop;
+};
+
+__device__ __forceinline__ UnitInfo unit_info(const LossArgs &a, int u) {
+    UnitInfo r;
+    const int e = a.frontier[u >> 1];
+    const int side = u & 1;
+    r.x = side ? a.ev[e] : a.eu[e];
+    r.y = side ? a.eu[e] : a.ev[e];
+    r.rb = a.row_ptr[r.y];
+    r.start = (side == 0) ? r.rb - 1 : r.rb;
+    r.stop = (a.h < 2) ? ((side == 0) ? r.rb : r.rb) : a.row_ptr[r.y + 1];
+    return r;
+}
+
+// Splits the frontier's edge sides into detection items of at most 32 pairs (one warp
+// each), so a hub row is spread over many warps.  Sides that do not fit the item list are
+// left to the next slot of the round (resume point).
+__global__ void k_pair_items(LossArgs a) {
+    DevStatus *st = a.st;
+    if (st->alive == 0) return;
+    const int units = 2 * st->nF, u0 = st->unit_begin;
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    for (int b = u0 + blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < units; b += stride) {
+        const int u = b + lane;
+        int nch = 0, start = 0;
+        if (u < units) {
+            const UnitInfo r = unit_info(a, u);
+            start = r.start;
+            nch = (r.stop - r.start + 31) >> 5;
+        }
+        int incl = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        int base = 0;
+        if (lane == 31 && tot) base = atomicAdd(&st->npitems, tot);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        const int first = base + incl - nch;
+        const bool fits = first + nch <= a.pitems_cap;
+        if (!fits && nch) atomicMin(&st->overflow_unit, u);
+        for (int c = 0; c < nch && first + c < a.pitems_cap; c++)
+            a.pitems[first + c] = fits ? make_int2(u, start + 32 * c) : make_int2(-1, 0);
+    }
+}
+
+// Loss detection, one warp per item: lane i tests the pair of slot item.y + i.  A pair is
+// kept if its endpoints are adjacent or (h = 2) share an alive neighbour; lanes whose test
+// needs a long row scan hand it to the whole warp, one pair after the other.
 __global__ void __launch_bounds__(kBlock) k_loss_detect(LossArgs a) {
     __shared__ unsigned long long s_pairs, s_reads;
     DevStatus *st = a.st;
@@ -147,65 +295,50 @@ __global__ void __launch_bounds__(kBlock) k_loss_detect(LossArgs a) {
         s_reads = 0ull;
     }
     __syncthreads();
-    unsigned long long reads_total = 0ull;
-    const int nF = st->nF, round = st->round, u0 = st->unit_begin;
+    const int nitems = min(st->npitems, a.pitems_cap), round = st->round;
     const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    unsigned long long pairs = 0ull;
-    for (int u = u0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); u < 2 * nF; u += nwarps) {
-        const int e = a.frontier[u >> 1];
-        const int side = u & 1;
-        const int x = side ? a.ev[e] : a.eu[e];
-        const int y = side ? a.eu[e] : a.ev[e];
-        const int rb = a.row_ptr[y], re = a.row_ptr[y + 1];
-        const int start = (side == 0) ? rb - 1 : rb;  // slot rb-1 stands for the pair {x,y}
-        if (a.h < 2 && side == 1) continue;           // h = 1: only {a,b} can be lost
-        const int stop = (a.h < 2) ? rb : re;
-        for (int s0 = start; s0 < stop; s0 += 32) {
-            const int s = s0 + lane;
-            int z = -1;
-            unsigned reads = 0;
-            if (s < stop) {
-                if (s < rb) {
-                    z = y;
-                } else {
-                    const int c = a.col[s];
-                    reads += 2;
-                    if (c != x) {
-                        if (a.col_live[s] >= 0) z = c;
-                        else if (a.stamp[a.slot_eid[s]] == round) z = c;
-                        reads += (a.col_live[s] >= 0) ? 0 : 2;
+    unsigned long long pairs = 0ull, reads_total = 0ull;
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nwarps) {
+        const int2 item = a.pitems[it];
+        const int u = item.x;
+        if (u < 0) continue;
+        const UnitInfo r = unit_info(a, u);
+        const int sl = item.y + lane;
+        int z = -1;
+        unsigned reads = 0;
+        if (sl < r.stop) {
+            if (sl < r.rb) {
+                z = r.y;
+            } else {
+                const int c = a.col[sl];
+                reads += 2;
+                if (c != r.x) {
+                    if (a.col_live[sl] >= 0) {
+                        z = c;
+                    } else {
+                        reads += 2;
+                        if (a.stamp[a.slot_eid[sl]] == round) z = c;
                     }
-                }
-            }
-            bool lost = false;
-            if (z >= 0) {
-                pairs++;
-                lost = !within_h(a, x, z, reads);
-            }
-            reads_total += reads;
-            // a pair whose stored bit is clear was handled by an earlier batch of this round
-            if (lost && ball_contains(a, x, z, reads)) {
-                const int idx = atomicAdd(&st->nlost, 1);  // reserve the record first
-                if (idx >= a.lost_max) {
-                    atomicMin(&st->overflow_unit, u);       // resume here in the next slot
-                } else {
-                    const unsigned long long key = pair_key(x, z);
-                    unsigned long long slot = mix64(key) & a.cap_mask;
-                    int4 rec = make_int4(-1, -1, -1, 0);    // null record: pair already held
-                    for (unsigned long long probe = 0; probe <= a.cap_mask; probe++) {
-                        const unsigned long long prev = atomicCAS(a.keys + slot, kEmpty, key);
-                        if (prev == kEmpty) {
-                            rec = make_int4(min(x, z), max(x, z), (int)slot, 0);
-                            break;
-                        }
-                        if (prev == key) break;
-                        slot = (slot + 1) & a.cap_mask;
-                    }
-                    a.lost[idx] = rec;
                 }
             }
         }
+        int state = kKept, p = r.x, q = z;
+        if (z >= 0) {
+            pairs++;
+            state = pair_quick(a, p, q, reads);
+        }
+        unsigned hard = __ballot_sync(0xffffffffu, state == kHard);
+        while (hard) {
+            const int leader = __ffs(hard) - 1;
+            hard &= hard - 1;
+            const int hp = __shfl_sync(0xffffffffu, p, leader);
+            const int hq = __shfl_sync(0xffffffffu, q, leader);
+            const bool kept = warp_common_neighbour(a, hp, hq, reads);
+            if (lane == leader) state = kept ? kKept : kLost;
+        }
+        if (state == kLost) record_lost(a, st, r.x, z, u, reads);
+        reads_total += reads;
     }
     for (int o = 16; o > 0; o >>= 1) {
         pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
@@ -222,9 +355,50 @@ __global__ void __launch_bounds__(kBlock) k_loss_detect(LossArgs a) {
     }
 }
 
-// Support updates for every directed loss (v loses w), one warp per loss, lanes over v's
-// alive edges (v,z).  PASS 0 (stored balls still old) handles edges with v < z and tests
-// w in B_old(z); PASS 1 (after the clears) handles v > z and tests w in B_new(z).
+// Splits every directed loss (v loses w) into update items of at most 32 of v's slots.
+// The detection reserved the work, so the item list always has room.  Also counts, once
+// per round and vertex, the alive edges whose support the updates bring up to date.
+__global__ void k_loss_items(LossArgs a) {
+    DevStatus *st = a.st;
+    if (st->alive == 0) return;
+    const int nd = 2 * min(st->nlost, a.lost_max), round = st->round;
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    unsigned long long touched = 0ull;
+    for (int b = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < nd; b += stride) {
+        const int d = b + lane;
+        int nch = 0, rb = 0;
+        if (d < nd) {
+            const int4 L = a.lost[d >> 1];
+            if (L.x >= 0) {
+                const int v = (d & 1) ? L.y : L.x;
+                rb = a.row_ptr[v];
+                nch = (a.row_ptr[v + 1] - rb + 31) >> 5;
+                if (atomicExch(a.vtouch + v, round) != round) touched += a.deg_alive[v];
+            }
+        }
+        int incl = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        int base = 0;
+        if (lane == 31 && tot) base = atomicAdd(&st->nuitems, tot);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        const int first = base + incl - nch;
+        for (int c = 0; c < nch && first + c < a.uitems_cap; c++)
+            a.uitems[first + c] = make_int2(d, rb + 32 * c);
+    }
+    for (int o = 16; o > 0; o >>= 1) touched += __shfl_xor_sync(0xffffffffu, touched, o);
+    if (lane == 0 && touched) atomicAdd((unsigned long long *)&st->st_recomputed, touched);
+}
+
+// Support updates, one warp per item (a directed loss v loses w, and 32 of v's slots).
+// PASS 0 (stored balls still old) handles edges (v,z) with v < z and tests w in B_old(z);
+// PASS 1 (after the clears) handles v > z and tests w in B_new(z).  Distance is symmetric,
+// so w in B(z) is tested as z in B(w): all lanes read the same ball, at increasing z.
 template <int PASS>
 __global__ void __launch_bounds__(kBlock) k_loss_delta(LossArgs a) {
     __shared__ unsigned long long s_tests, s_bytes;
@@ -235,30 +409,27 @@ __global__ void __launch_bounds__(kBlock) k_loss_delta(LossArgs a) {
         s_bytes = 0ull;
     }
     __syncthreads();
-    unsigned long long bytes_total = 0ull;
-    const int nlost = min(st->nlost, a.lost_max), round = st->round;
+    const int nitems = min(st->nuitems, a.uitems_cap);
     const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    unsigned long long tests = 0ull;
-    for (int d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < 2 * nlost; d += nwarps) {
-        const int4 L = a.lost[d >> 1];
-        if (L.x < 0) continue;
-        const int v = (d & 1) ? L.y : L.x;
-        const int w = (d & 1) ? L.x : L.y;
+    unsigned long long tests = 0ull, bytes_total = 0ull;
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nwarps) {
+        const int2 item = a.uitems[it];
+        const int4 L = a.lost[item.x >> 1];
+        const int v = (item.x & 1) ? L.y : L.x;
+        const int w = (item.x & 1) ? L.x : L.y;
+        const int2 wmeta = a.ball_meta[w];
         const int re = a.row_ptr[v + 1];
-        unsigned bytes = (lane == 0) ? 24u : 0u;  // the loss record and v's row bounds
-        for (int s = a.row_ptr[v] + lane; s < re; s += 32) {
-            const int z = a.col_live[s];
+        const int sl = item.y + lane;
+        unsigned bytes = (lane == 0) ? 32u : 0u;  // item, loss record, row end, ball metadata
+        if (sl < re) {
+            const int z = a.col_live[sl];
             bytes += 4;
-            if (z < 0) continue;
-            const int e = a.slot_eid[s];
-            bytes += 4;
-            if (PASS == 0) a.edge_touch[e] = round;
-            if (PASS == 0 ? (v < z) : (v > z)) {
+            if (z >= 0 && (PASS == 0 ? (v < z) : (v > z))) {
                 tests++;
-                if (ball_contains(a, z, w, bytes)) {
-                    atomicSub(a.sup + e, 1);
-                    bytes += 8;
+                if (ball_contains_meta(a, wmeta, z, bytes)) {
+                    atomicSub(a.sup + a.slot_eid[sl], 1);
+                    bytes += 12;
                 }
             }
         }
@@ -289,8 +460,9 @@ __global__ void k_loss_apply(LossArgs a) {
         if (L.x < 0) continue;
         const int v = (d & 1) ? L.y : L.x;
         const int w = (d & 1) ? L.x : L.y;
-        const int nw = a.ball_nw[v];
-        const int64_t off = a.ball_off[v];
+        const int2 meta = a.ball_meta[v];
+        const int nw = meta.y;
+        const int64_t off = (int64_t)(unsigned)meta.x << 2;
         const uint32_t bit = 1u << (w & 31);
         const uint32_t wi = (uint32_t)(w >> 5);
         uint32_t *word = nullptr;
@@ -342,11 +514,21 @@ LossArgs loss_args(Handle *H) {
     a.pool = w.pool;
     a.ball_off = w.ball_off;
     a.ball_nw = w.ball_nw;
+    a.ball_meta = w.ball_meta;
     a.ball_size = w.ball_size;
     a.keys = w.lost_keys;
     a.lost = w.lost;
     a.sup = w.sup;
-    a.edge_touch = w.edge_touch;
+    a.vtouch = w.edge_touch;
+    a.deg_alive = w.deg_alive;
+    a.pitems_cap = (int32_t)w.pitems_cap;
+    a.pitems = w.pitems;
+    a.uitems_cap = (int32_t)w.uitems_cap;
+    a.uitems = w.uitems;
+    a.upd_budget = w.upd_budget;
+    a.hub_slot = w.hub_slot;
+    a.hub_bits = w.hub_bits;
+    a.Wpad = w.Wpad;
     a.st = w.status;
     return a;
 }
@@ -359,12 +541,14 @@ htd_status enqueue_loss_kernels(Handle *H, cudaStream_t s, int64_t *launches, cu
                                 unsigned record_flags) {
     LossArgs a = loss_args(H);
     const int grid = H->num_sms * 8;
+    k_pair_items<<<H->num_sms * 4, kBlock, 0, s>>>(a);
     k_loss_detect<<<grid, kBlock, 0, s>>>(a);
     if (ev_mid) cudaEventRecordWithFlags(ev_mid, s, record_flags);
+    k_loss_items<<<H->num_sms * 4, kBlock, 0, s>>>(a);
     k_loss_delta<0><<<grid, kBlock, 0, s>>>(a);
     k_loss_apply<<<grid, kBlock, 0, s>>>(a);
     k_loss_delta<1><<<grid, kBlock, 0, s>>>(a);
-    *launches += 4;
+    *launches += 6;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_last_error(std::string("enqueue_loss_kernels: ") + cudaGetErrorString(e));

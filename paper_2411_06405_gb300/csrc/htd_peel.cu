@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "htd_internal.h"
 #include "htd_scan.cuh"
@@ -47,6 +48,7 @@ struct BallArgs {
     int32_t *ball_need;
     int32_t *ball_size;
     int32_t *ball_nw;
+    int2 *ball_meta;
     const int32_t *cand_list;
     int32_t *changed_list;
     int32_t *changed_stamp;
@@ -247,6 +249,7 @@ __global__ void __launch_bounds__(kBlock) k_ball(BallArgs a) {
                                                   (unsigned long long)size);
                 a.ball_size[x] = size;
                 a.ball_nw[x] = dense ? -1 : nzw;
+                a.ball_meta[x] = make_int2((int)(off >> 2), dense ? -1 : nzw);
                 if (MODE == kModeRebuild) {
                     a.changed_stamp[x] = st->round;
                     a.changed_list[atomicAdd(&st->nchanged, 1)] = x;
@@ -478,7 +481,8 @@ __global__ void k_remove(const int32_t *__restrict__ frontier, DevStatus *st,
                          const int32_t *__restrict__ slot_lo, const int32_t *__restrict__ slot_hi,
                          int32_t *__restrict__ sup, int32_t *__restrict__ truss,
                          int32_t *__restrict__ stamp, int32_t *__restrict__ col_live,
-                         int32_t *__restrict__ deg_alive) {
+                         int32_t *__restrict__ deg_alive, const int32_t *__restrict__ hub_slot,
+                         uint32_t *__restrict__ hub_bits, int32_t Wpad) {
     if (st->alive == 0 || st->cont) return;  // a continued round removed its frontier already
     const int nF = st->nF, k = st->k, round = st->round;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
@@ -491,6 +495,29 @@ __global__ void k_remove(const int32_t *__restrict__ frontier, DevStatus *st,
         col_live[slot_hi[e]] = ~u;
         atomicSub(&deg_alive[u], 1);
         atomicSub(&deg_alive[v], 1);
+        if (hub_slot) {  // alive-adjacency sets of high-degree endpoints
+            const int hu = hub_slot[u], hv = hub_slot[v];
+            if (hu >= 0) atomicAnd(hub_bits + (int64_t)hu * Wpad + (v >> 5), ~(1u << (v & 31)));
+            if (hv >= 0) atomicAnd(hub_bits + (int64_t)hv * Wpad + (u >> 5), ~(1u << (u & 31)));
+        }
+    }
+}
+
+// Alive-adjacency n-bit sets of the high-degree vertices (all edges alive), block per hub.
+__global__ void __launch_bounds__(kBlock) k_hub_init(const int32_t *__restrict__ hub_list, int32_t nhub,
+                                                    const int32_t *__restrict__ row_ptr,
+                                                    const int32_t *__restrict__ col,
+                                                    uint32_t *__restrict__ hub_bits, int32_t Wpad) {
+    for (int hb = blockIdx.x; hb < nhub; hb += gridDim.x) {
+        uint32_t *bits = hub_bits + (int64_t)hb * Wpad;
+        for (int i = threadIdx.x; i < Wpad; i += kBlock) bits[i] = 0u;
+        __syncthreads();
+        const int x = hub_list[hb];
+        for (int s = row_ptr[x] + threadIdx.x; s < row_ptr[x + 1]; s += kBlock) {
+            const int y = col[s];
+            atomicOr(bits + (y >> 5), 1u << (y & 31));
+        }
+        __syncthreads();
     }
 }
 
@@ -577,6 +604,9 @@ __global__ void __launch_bounds__(kBlock) k_minreduce(const int32_t *__restrict_
         for (int j = 0; j < kMaxH; j++) st->cand_cnt[j] = 0;
         st->nchanged = 0;
         st->nlost = 0;
+        st->npitems = 0;
+        st->nuitems = 0;
+        st->upd_work = 0;
         st->nitems = 0;
         st->q_ball = 0;
         st->q_items = 0;
@@ -621,6 +651,7 @@ BallArgs ball_args(Handle *H) {
     a.ball_need = w.ball_need;
     a.ball_size = w.ball_size;
     a.ball_nw = w.ball_nw;
+    a.ball_meta = w.ball_meta;
     a.cand_list = w.cand_list;
     a.changed_list = w.changed_list;
     a.changed_stamp = w.changed_stamp;
@@ -661,6 +692,7 @@ void free_work(PeelWork *w) {
     cudaFree(w->ball_need);
     cudaFree(w->ball_size);
     cudaFree(w->ball_nw);
+    cudaFree(w->ball_meta);
     cudaFree(w->col_live);
     cudaFree(w->deg_alive);
     cudaFree(w->sup);
@@ -676,6 +708,11 @@ void free_work(PeelWork *w) {
     cudaFree(w->lost_keys);
     cudaFree(w->lost);
     cudaFree(w->edge_touch);
+    cudaFree(w->hub_slot);
+    cudaFree(w->hub_list);
+    cudaFree(w->hub_bits);
+    cudaFree(w->pitems);
+    cudaFree(w->uitems);
     cudaFree(w->scan_tmp);
     cudaFree(w->status);
     if (w->status_host) cudaFreeHost(w->status_host);
@@ -726,6 +763,7 @@ htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) 
     HTD_CHECK(alloc_n(&w.ball_need, n));
     HTD_CHECK(alloc_n(&w.ball_size, n));
     HTD_CHECK(alloc_n(&w.ball_nw, n));
+    HTD_CHECK(alloc_n(&w.ball_meta, n));
     HTD_CHECK(alloc_n(&w.col_live, 2 * m));
     HTD_CHECK(alloc_n(&w.deg_alive, n));
     HTD_CHECK(alloc_n(&w.sup, m));
@@ -752,7 +790,43 @@ htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) 
         w.lost_max = cap / 2;
         HTD_CHECK(alloc_n(&w.lost_keys, cap));
         HTD_CHECK(alloc_n(&w.lost, w.lost_max));
-        HTD_CHECK(alloc_n(&w.edge_touch, m));
+        HTD_CHECK(alloc_n(&w.edge_touch, n));
+        // work items of the loss detection and of the support updates (per batch)
+        w.pitems_cap = (int64_t)1 << 22;
+        w.upd_budget = (int64_t)1 << 26;  // adjacency slots the updates of one batch may visit
+        w.uitems_cap = 2 * w.lost_max + w.upd_budget / 32 + 1024;
+        HTD_CHECK(alloc_n(&w.pitems, w.pitems_cap));
+        HTD_CHECK(alloc_n(&w.uitems, w.uitems_cap));
+        // alive-adjacency n-bit sets: every vertex of degree >= T, the smallest power of two
+        // for which they fit in min(16 GiB, a quarter of the free device memory)
+        std::vector<int32_t> rp(n + 1);
+        HTD_CHECK(cudaMemcpy(rp.data(), g.row_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        size_t free_b = 0, total_b = 0;
+        HTD_CHECK(cudaMemGetInfo(&free_b, &total_b));
+        const int64_t budget_words = std::min<int64_t>((int64_t)1 << 32, (int64_t)(free_b / 16));
+        int32_t T = 1;
+        int64_t cnt = 0;
+        for (;; T *= 2) {
+            cnt = 0;
+            for (int64_t x = 0; x < n; x++) cnt += (rp[x + 1] - rp[x] >= T);
+            if (cnt * w.Wpad <= budget_words || T > (1 << 24)) break;
+        }
+        std::vector<int32_t> slot(n > 0 ? n : 1, -1), list;
+        for (int64_t x = 0; x < n; x++)
+            if (rp[x + 1] - rp[x] >= T) {
+                slot[x] = (int32_t)list.size();
+                list.push_back((int32_t)x);
+            }
+        w.nhub = (int32_t)list.size();
+        w.hub_min_deg = T;
+        HTD_CHECK(alloc_n(&w.hub_slot, n));
+        HTD_CHECK(cudaMemcpy(w.hub_slot, slot.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+        if (w.nhub > 0) {
+            HTD_CHECK(alloc_n(&w.hub_list, w.nhub));
+            HTD_CHECK(cudaMemcpy(w.hub_list, list.data(), w.nhub * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice));
+            HTD_CHECK(alloc_n(&w.hub_bits, (int64_t)w.nhub * w.Wpad));
+        }
     }
     w.incremental = incremental;
     HTD_CHECK(cudaMalloc(&w.scan_tmp, scan_temp_bytes(n + 1)));
@@ -781,8 +855,13 @@ htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
     HTD_CHECK(cudaMemsetAsync(w.changed_stamp, 0xff, (n > 0 ? n : 1) * sizeof(int32_t), s));
     HTD_CHECK(cudaMemsetAsync(w.stamp, 0xff, (m > 0 ? m : 1) * sizeof(int32_t), s));
     if (w.incremental) {
-        HTD_CHECK(cudaMemsetAsync(w.edge_touch, 0xff, (m > 0 ? m : 1) * sizeof(int32_t), s));
+        HTD_CHECK(cudaMemsetAsync(w.edge_touch, 0xff, (n > 0 ? n : 1) * sizeof(int32_t), s));
         HTD_CHECK(cudaMemsetAsync(w.lost_keys, 0xff, w.lost_cap * sizeof(unsigned long long), s));
+        if (w.nhub > 0) {
+            k_hub_init<<<std::min(w.nhub, H->num_sms * 8), kBlock, 0, s>>>(w.hub_list, w.nhub, g.row_ptr,
+                                                                        g.col, w.hub_bits, w.Wpad);
+            (*launches)++;
+        }
     }
     if (n > 0) {
         k_init_deg<<<std::min<int64_t>((n + kBlock - 1) / kBlock, H->num_sms * 8), kBlock, 0, s>>>(
@@ -805,6 +884,10 @@ htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
         int64_t total = 0;
         HTD_CHECK(cudaMemcpyAsync(&total, w.ball_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         HTD_CHECK(cudaStreamSynchronize(s));
+        if (total >= ((int64_t)1 << 33)) {
+            set_last_error("htd: h-hop balls need more than 32 GiB of storage");
+            return HTD_EUNSUPPORTED;
+        }
         if (total > w.pool_words) {
             cudaFree(w.pool);
             w.pool = nullptr;
@@ -873,14 +956,15 @@ htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent
     mark(1);
     if (w.incremental) {
         k_remove<<<gsmall, kBlock, 0, s>>>(w.frontier, w.status, g.eu, g.ev, g.slot_lo, g.slot_hi,
-                                           w.sup, w.truss, w.stamp, w.col_live, w.deg_alive);
+                                           w.sup, w.truss, w.stamp, w.col_live, w.deg_alive,
+                                           w.hub_slot, w.hub_bits, w.Wpad);
         mark(2);
         *launches += 2;
         htd_status ls = enqueue_loss_kernels(H, s, launches, evs ? evs[3] : nullptr, rec_flags);
         if (ls != HTD_OK) return ls;
         mark(4);
         mark(5);
-        k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 0, w.edge_touch);
+        k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 0, nullptr);
         mark(6);
         (*launches)++;
         HTD_CHECK(cudaGetLastError());
@@ -895,7 +979,8 @@ htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent
     }
     mark(2);
     k_remove<<<gsmall, kBlock, 0, s>>>(w.frontier, w.status, g.eu, g.ev, g.slot_lo, g.slot_hi,
-                                       w.sup, w.truss, w.stamp, w.col_live, w.deg_alive);
+                                       w.sup, w.truss, w.stamp, w.col_live, w.deg_alive, nullptr,
+                                       nullptr, 0);
     (*launches)++;
     mark(3);
     BallArgs ba = ball_args(H);
