@@ -242,7 +242,7 @@ def run_gpu(args, world, rank, local):
     def mean(key):
         return float(np.mean([s[key] for s in stats]))
 
-    rounds_timed = max(1, s0["timed_rounds"])
+    rounds_timed = max(1, s0["timed_slots"])
     # kernel classes of one step: (name, device ms per step, launches per step, alg bytes)
     ball_store_bytes = mean("alg_bytes_ball") / 2 if s0["incremental"] else None
     classes = [

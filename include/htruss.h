@@ -73,7 +73,8 @@ typedef struct htd_stats {
     int64_t member_tests;    /* incremental rounds: ball-membership tests of support updates */
     int64_t kernel_launches; /* kernels this library launched for the call */
     int64_t ball_pool_bytes; /* device bytes held by the h-hop balls */
-    int64_t timed_rounds;    /* rounds whose phases were timed */
+    int64_t timed_slots;     /* round slots timed (a slot runs one round or one batch of a
+                                continued round; slots after the last round are no-ops) */
     double alg_bytes_ball;   /* algorithmic bytes: ball builds (initial and rebuilds) */
     double alg_bytes_hsup;   /* algorithmic bytes: full h-support intersections */
     double alg_bytes_detect; /* algorithmic bytes: loss detection (incremental rounds) */

@@ -46,7 +46,7 @@ class HtdStats(ctypes.Structure):
         ("member_tests", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
         ("ball_pool_bytes", ctypes.c_int64),
-        ("timed_rounds", ctypes.c_int64),
+        ("timed_slots", ctypes.c_int64),
         ("alg_bytes_ball", ctypes.c_double),
         ("alg_bytes_hsup", ctypes.c_double),
         ("alg_bytes_detect", ctypes.c_double),

@@ -350,7 +350,6 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
                 set_last_error("htd_truss_decompose: no progress within the batch cap");
                 return HTD_ETIMEOUT;
             }
-            const int32_t rounds_before = w.status_host->round;
             if (use_graph) {
                 API_CHECK(cudaGraphLaunch(H->graph_exec, H->pstream));
                 launches += (int64_t)R * per_round;
@@ -374,8 +373,9 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
                 return es;
             }
             if (timing_ok) {
-                const int active = w.status_host->round - rounds_before;
-                for (int r = 0; r < active && r < R && timing_ok; r++) {
+                // every slot of the batch ran (continued rounds and the no-op slots after the
+                // last round included), so all of them are timed
+                for (int r = 0; r < R && timing_ok; r++) {
                     float t[htd::kRoundEvents - 1];
                     for (int q = 0; q + 1 < htd::kRoundEvents; q++) {
                         if (cudaEventElapsedTime(&t[q], evs[htd::kRoundEvents * r + q],
@@ -398,9 +398,9 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
                         local.ms_update += t[4];
                     }
                     local.ms_minreduce += t[5];
-                    local.timed_rounds += 1;
+                    local.timed_slots += 1;
                 }
-                if (!timing_ok) local.timed_rounds = -1;
+                if (!timing_ok) local.timed_slots = -1;
             }
             if (w.status_host->round > round_cap) {
                 cleanup_events();

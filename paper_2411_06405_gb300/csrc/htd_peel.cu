@@ -792,8 +792,10 @@ htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) 
         HTD_CHECK(alloc_n(&w.lost, w.lost_max));
         HTD_CHECK(alloc_n(&w.edge_touch, n));
         // work items of the loss detection and of the support updates (per batch)
-        w.pitems_cap = (int64_t)1 << 22;
-        w.upd_budget = (int64_t)1 << 26;  // adjacency slots the updates of one batch may visit
+        // (sized with the graph: 2m adjacency slots)
+        w.pitems_cap = std::min<int64_t>((int64_t)1 << 22, std::max<int64_t>(4096, 2 * m));
+        // adjacency slots the updates of one batch may visit
+        w.upd_budget = std::min<int64_t>((int64_t)1 << 28, std::max<int64_t>(1 << 16, 64 * m));
         w.uitems_cap = 2 * w.lost_max + w.upd_budget / 32 + 1024;
         HTD_CHECK(alloc_n(&w.pitems, w.pitems_cap));
         HTD_CHECK(alloc_n(&w.uitems, w.uitems_cap));

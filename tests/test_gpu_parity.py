@@ -238,8 +238,8 @@ def test_graph_and_direct_launch_agree_and_repeat(htd, oracle_mod):
     assert torch.equal(t1, t2) and torch.equal(t1, t3) and torch.equal(t1, t5)
     assert torch.equal(st1, st5)  # same level-synchronous schedule
     assert s1["rounds"] == s2["rounds"] == s3["rounds"] == s5["rounds"]
-    assert s3["timed_rounds"] == s3["rounds"] and s3["ms_find"] > 0
-    assert s5["timed_rounds"] == s5["rounds"] and s5["ms_ball"] > 0
+    assert s3["timed_slots"] >= s3["rounds"] and s3["ms_find"] > 0
+    assert s5["timed_slots"] >= s5["rounds"] and s5["ms_ball"] > 0
     assert s1["incremental"] == 1 and s5["incremental"] == 0
     # changing h on the same handle and coming back
     t_h3, _, _ = htd.htd_truss_decompose(g, 3)
