@@ -151,6 +151,31 @@ htd_status htd_truss_decompose_host(int32_t n, const int32_t *src_host,
                                     int32_t *eu_host, int32_t *ev_host, int32_t *truss_host,
                                     int64_t *m_out, htd_stats *stats, void *stream);
 
+/* h-support of every edge without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory themselves
+ * (code running inside an allocator or memory-pool callback, or under an external budget
+ * that already owns all device memory).  The caller passes the normalised graph (the
+ * arrays htd_csr and htd_edges return) and the output; the kernel's scratch is one
+ * static device array of 32 MiB that every GPU loading this library keeps until the
+ * process exits.
+ *   n                        vertex count, n <= HTD_STATIC_MAX_N (two n-bit sets of a
+ *                            block must fit in shared memory).
+ *   row_ptr_dev, col_dev     CSR: n+1 offsets, 2m neighbours sorted within each row.
+ *   eu_dev, ev_dev           the m canonical edges.
+ *   sup_dev                  output, m int32: sup(e,h) as htd_h_support computes it.
+ * Unlike the other calls this one only enqueues work on `stream` (NULL = legacy default
+ * stream) and returns; the result is ready when the stream reaches that point.  The first
+ * call on a device looks up the scratch array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call shares the one scratch
+ * array and reuses what the previous call left there: calls that overlap on the GPU (two
+ * streams, or two threads) race and must be serialised by the caller.  Errors: EINVAL for
+ * a NULL pointer or h outside [1, HTD_MAX_H], EUNSUPPORTED for n > HTD_STATIC_MAX_N or, at
+ * h >= 3, when one block's level lists (2n int32) exceed the scratch, ECUDA otherwise. */
+#define HTD_STATIC_MAX_N 786432
+htd_status htd_h_support_static(int32_t n, const int32_t *row_ptr_dev, const int32_t *col_dev,
+                                int64_t m, const int32_t *eu_dev, const int32_t *ev_dev,
+                                int32_t h, int32_t *sup_dev, void *stream);
+
 /* Frees the handle and every device buffer it owns (NULL is ignored). */
 void htd_graph_free(htd_graph *g);
 

@@ -25,7 +25,8 @@ __all__ = [
     "HTD_MAX_H", "HTD_MAX_N", "HTD_OPT_NO_GRAPH", "HTD_OPT_REBUILD", "HTD_OPT_TIMING",
     "HTD_OPT_TINY_LOSS_TABLE", "HtdError", "HtdStats",
     "Graph", "htd_build_csr", "htd_graph_info", "htd_edges", "htd_csr", "htd_h_support",
-    "htd_truss_decompose", "htd_truss_decompose_host", "htd_graph_free", "library_path",
+    "htd_truss_decompose", "htd_truss_decompose_host", "htd_h_support_static", "htd_graph_free",
+    "library_path",
 ]
 
 
@@ -182,6 +183,15 @@ def htd_truss_decompose_host(n: int, src, dst, h: int, out_eu=None, out_ev=None,
     _lib.check(st, "htd_truss_decompose_host")
     mm = int(m.value)
     return out_eu[:mm], out_ev[:mm], out_truss[:mm], stats.as_dict()
+
+
+def htd_h_support_static(n: int, row_ptr, col, eu, ev, h: int, out, stream=None):
+    """Allocation-free h-support on caller-provided CUDA tensors (CSR + edges + output).
+    Enqueues on the stream and returns without waiting."""
+    _lib.check(_lib.load().htd_h_support_static(int(n), _ptr(row_ptr), _ptr(col), int(eu.numel()),
+                                                _ptr(eu), _ptr(ev), int(h), _ptr(out),
+                                                _stream_handle(stream)), "htd_h_support_static")
+    return out
 
 
 def htd_graph_free(g: Graph):

@@ -18,6 +18,7 @@ HTD_EOVERFLOW = 5
 HTD_EUNSUPPORTED = 6
 HTD_MAX_H = 8
 HTD_MAX_N = 1600000
+HTD_STATIC_MAX_N = 786432
 HTD_OPT_TIMING = 1
 HTD_OPT_NO_GRAPH = 2
 HTD_OPT_REBUILD = 4
@@ -28,6 +29,7 @@ EXPORTED = (
     "htd_build_csr", "htd_graph_info", "htd_edges", "htd_csr", "htd_h_support",
     "htd_truss_decompose", "htd_truss_decompose_ex", "htd_truss_decompose_host",
     "htd_graph_free", "htd_kernel_launch_count", "htd_status_string", "htd_last_error",
+    "htd_h_support_static",
 )
 
 
@@ -103,6 +105,7 @@ def load():
                                          ctypes.c_int),
             "htd_graph_free": ([p], None),
             "htd_kernel_launch_count": ([], i64),
+            "htd_h_support_static": ([i32, p, p, i64, p, p, i32, p, p], ctypes.c_int),
             "htd_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "htd_last_error": ([], ctypes.c_char_p),
         }
