@@ -32,6 +32,7 @@ WORKLOADS = {
     "dcsbm_n200k_h2": ("dcsbm_n200k", 2),
     "dcsbm_n200k_h3": ("dcsbm_n200k", 3),
     "er_n2000_h2": ("er_n2000", 2),
+    "rmat_s16_h2": ("rmat_s16", 2),
 }
 METRIC = "edges decomposed/sec"
 UNIT = "edges/s"
@@ -217,21 +218,22 @@ def run_gpu(args, world, rank, local):
     value = world * m * args.steps / (t_max / 1e3)
 
     # end to end through the host-buffer entry point (pinned buffers, copies inside)
-    src_h = torch.from_numpy(spec.src).pin_memory()
-    dst_h = torch.from_numpy(spec.dst).pin_memory()
+    e2e_value, e2e_ms = None, []
     k = spec.src.size
-    out = [torch.empty(k, dtype=torch.int32).pin_memory() for _ in range(3)]
-    htd.htd_truss_decompose_host(spec.n, src_h, dst_h, h, *out)  # warm
-    e2e_ms = []
-    for _ in range(max(1, min(args.steps, 3))):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        eu, ev_, tr, st_e2e = htd.htd_truss_decompose_host(spec.n, src_h, dst_h, h, *out)
-        b.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms.append(a.elapsed_time(b))
-    e2e_value = m / (float(np.mean(e2e_ms)) / 1e3)
+    if not args.no_e2e:
+        src_h = torch.from_numpy(spec.src).pin_memory()
+        dst_h = torch.from_numpy(spec.dst).pin_memory()
+        out = [torch.empty(k, dtype=torch.int32).pin_memory() for _ in range(3)]
+        htd.htd_truss_decompose_host(spec.n, src_h, dst_h, h, *out)  # warm
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            htd.htd_truss_decompose_host(spec.n, src_h, dst_h, h, *out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+        e2e_value = m / (float(np.mean(e2e_ms)) / 1e3)
 
     if rank != 0:
         return
@@ -296,8 +298,9 @@ def run_gpu(args, world, rank, local):
                      "traffic": traffic, "peak_source": peak_kind,
                      "alg_bytes_per_launch": (k_bytes / k_launches) if k_bytes else None,
                      "launches_per_step": k_launches, "ms_per_launch": k_ms / k_launches},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(8 * k),
-                "d2h_bytes_per_step": int(12 * m), "ms_per_step": float(np.mean(e2e_ms))},
+        "e2e": None if e2e_value is None else {
+            "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(8 * k),
+            "d2h_bytes_per_step": int(12 * m), "ms_per_step": float(np.mean(e2e_ms))},
         "gpu_launches": int(launches // args.steps),
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
@@ -314,6 +317,7 @@ def main():
     ap.add_argument("--workload", default="rmat_s18_h2", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if world > 1:

@@ -87,6 +87,10 @@ typedef struct htd_stats {
     float ms_ball;           /* rounds: ball rebuilds (rebuild variant) */
     float ms_update;         /* rounds: support recomputation or incremental updates */
     float ms_minreduce;      /* rounds: min alive support + alive count */
+    float ms_round_kernel;   /* persistent round kernel: device time of all its launches
+                                (always measured; the phase times above then come from the
+                                GPU's global timer, as seen by one block) */
+    int32_t round_kernel_launches;
     int32_t incremental;     /* 1 if the rounds used incremental support updates */
     int32_t reserved;
 } htd_stats;
@@ -96,6 +100,8 @@ typedef struct htd_stats {
 #define HTD_OPT_NO_GRAPH 2u  /* launch each peel round directly instead of via a CUDA graph */
 #define HTD_OPT_REBUILD 4u   /* h <= 2: rebuild shrunk balls and recompute their edges' support
                                 instead of the incremental lost-pair updates (same results) */
+#define HTD_OPT_GRAPH_ROUNDS 16u   /* h <= 2: one launch per phase in a CUDA graph of 16 rounds,
+                                       instead of the persistent round kernel (same results) */
 #define HTD_OPT_TINY_LOSS_TABLE 8u  /* h <= 2: 128-slot lost-pair table, so that rounds run in
                                        many batches (a test of that path; slow) */
 

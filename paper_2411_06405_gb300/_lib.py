@@ -23,6 +23,7 @@ HTD_OPT_TIMING = 1
 HTD_OPT_NO_GRAPH = 2
 HTD_OPT_REBUILD = 4
 HTD_OPT_TINY_LOSS_TABLE = 8
+HTD_OPT_GRAPH_ROUNDS = 16
 
 # every symbol include/htruss.h declares
 EXPORTED = (
@@ -61,6 +62,8 @@ class HtdStats(ctypes.Structure):
         ("ms_ball", ctypes.c_float),
         ("ms_update", ctypes.c_float),
         ("ms_minreduce", ctypes.c_float),
+        ("ms_round_kernel", ctypes.c_float),
+        ("round_kernel_launches", ctypes.c_int32),
         ("incremental", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
     ]

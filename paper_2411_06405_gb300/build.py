@@ -20,6 +20,8 @@ LIB = os.path.join(BUILD, "libhtruss.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Extra nvcc flags of single translation units (none at present).
+PER_FILE_FLAGS = {}
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE]
 
@@ -52,7 +54,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     jobs = []
     for s, o in zip(srcs, objs):
         if force or _stale(o, [s] + headers):
-            jobs.append([nvcc()] + ARCH + flags + ["-c", s, "-o", o])
+            extra = []
+            if os.path.basename(s) in PER_FILE_FLAGS:
+                extra = PER_FILE_FLAGS[os.path.basename(s)]
+            jobs.append([nvcc()] + ARCH + flags + extra + ["-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))

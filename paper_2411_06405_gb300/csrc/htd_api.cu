@@ -302,7 +302,63 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
         for (auto &e : evs) API_CHECK(cudaEventCreate(&e));
     }
     const int per_round = incremental ? 9 : h + 6;
-    if (w.status_host->alive > 0) {
+    const bool persistent = incremental && (flags & HTD_OPT_GRAPH_ROUNDS) == 0;
+    if (persistent && w.status_host->alive > 0) {
+        // one cooperative launch runs up to kPersistentSlots round slots; the host checks the
+        // status block between launches
+        constexpr int kPersistentSlots = 4096;
+        const int64_t slot_cap = H->g.m + w.status_host->st_ball_total / 2 + 2;
+        const int64_t launch_cap = slot_cap / kPersistentSlots + 3;
+        cudaEvent_t p0 = nullptr, p1 = nullptr;
+        API_CHECK(cudaEventCreate(&p0));
+        API_CHECK(cudaEventCreate(&p1));
+        int64_t nlaunch = 0;
+        htd_status ps = HTD_OK;
+        while (ps == HTD_OK && w.status_host->alive > 0) {
+            if (++nlaunch > launch_cap) {
+                set_last_error("htd_truss_decompose: no progress within the slot cap");
+                ps = HTD_ETIMEOUT;
+                break;
+            }
+            if (cudaEventRecord(p0, H->pstream) != cudaSuccess) ps = HTD_ECUDA;
+            if (ps == HTD_OK) ps = htd::launch_persistent_rounds(H, H->pstream, kPersistentSlots, &launches);
+            if (ps == HTD_OK && cudaEventRecord(p1, H->pstream) != cudaSuccess) ps = HTD_ECUDA;
+            count_launches();
+            if (ps != HTD_OK) break;
+            if (cudaMemcpyAsync(w.status_host, w.status, sizeof(htd::DevStatus),
+                                cudaMemcpyDeviceToHost, H->pstream) != cudaSuccess ||
+                cudaStreamSynchronize(H->pstream) != cudaSuccess) {
+                set_last_error(std::string("htd_truss_decompose: ") +
+                               cudaGetErrorString(cudaGetLastError()));
+                ps = HTD_ECUDA;
+                break;
+            }
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p0, p1) == cudaSuccess) {
+                local.ms_round_kernel += ms;
+                local.round_kernel_launches += 1;
+            }
+            if (w.status_host->err & htd::kErrBarrierTimeout) {
+                set_last_error("htd_truss_decompose: a grid barrier of the round kernel timed out");
+                ps = HTD_ETIMEOUT;
+                break;
+            }
+            ps = check_status_err(w.status_host);
+        }
+        cudaEventDestroy(p0);
+        cudaEventDestroy(p1);
+        if (ps != HTD_OK) {
+            cleanup_events();
+            return ps;
+        }
+        const htd::DevStatus *sh = w.status_host;
+        local.ms_select = sh->st_phase_ns[0] * 1e-6f;
+        local.ms_find = (sh->st_phase_ns[1] + sh->st_phase_ns[2]) * 1e-6f;
+        local.ms_update = (sh->st_phase_ns[3] + sh->st_phase_ns[4] + sh->st_phase_ns[5] +
+                           sh->st_phase_ns[6]) * 1e-6f;
+        local.ms_minreduce = sh->st_phase_ns[7] * 1e-6f;
+        local.timed_slots = sh->st_slots;
+    } else if (w.status_host->alive > 0) {
         if (use_graph && (!H->graph_exec || H->graph_h != h || H->graph_rounds != (timing ? -R : R) ||
                           H->graph_incremental != incremental)) {
             destroy_graph(H);

@@ -47,6 +47,10 @@ struct DevStatus {
     int32_t nuitems;           // support update items of the current batch
     int32_t pad1;
     long long upd_work;        // adjacency slots reserved for the batch's updates
+    unsigned bar_count;        // grid barrier of the persistent round kernel
+    unsigned bar_gen;
+    long long st_slots;        // round slots run by the persistent kernel
+    unsigned long long st_phase_ns[8];  // persistent kernel: time per phase (block 0's view)
     int64_t st_ball_total;     // sum of the initial ball sizes
     int64_t st_pairs;          // candidate pairs tested
     int64_t st_lost;           // lost pairs
@@ -59,6 +63,7 @@ enum : int32_t {
     kErrBallGrew = 1,        // a rebuilt ball was larger than before (cannot happen)
     kErrBallCapacity = 2,    // a ball did not fit its storage (cannot happen)
     kErrListOverflow = 4,    // a per-block BFS list overflowed (cannot happen)
+    kErrBarrierTimeout = 16, // a grid barrier gave up waiting
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -106,6 +106,9 @@ htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
 constexpr int kRoundEvents = 7;
 htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t *evs);
 
+// Persistent kernel running up to max_slots incremental round slots (htd_loss.cu).
+htd_status launch_persistent_rounds(Handle *H, cudaStream_t s, int max_slots, int64_t *launches);
+
 // Incremental support updates of one round, h <= 2 (htd_loss.cu).
 htd_status enqueue_loss_kernels(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t ev_mid,
                                 unsigned record_flags);

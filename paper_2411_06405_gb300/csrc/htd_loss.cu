@@ -25,6 +25,7 @@
 #include <cstdint>
 
 #include "htd_internal.h"
+#include "htd_round.cuh"
 
 namespace htd {
 namespace {
@@ -33,6 +34,15 @@ constexpr int kBlock = 256;
 constexpr unsigned long long kEmpty = ~0ull;
 
 struct LossArgs {
+    int64_t m;
+    const int32_t *slot_lo;
+    const int32_t *slot_hi;
+    int32_t *truss;
+    int32_t *stamp_w;
+    int32_t *frontier_w;
+    int32_t *col_live_w;
+    int32_t *deg_alive_w;
+    uint32_t *hub_bits_w;
     int32_t h;
     int32_t lost_max;
     unsigned long long cap_mask;
@@ -78,6 +88,13 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
     k *= 0xc4ceb9fe1a85ec53ull;
     k ^= k >> 33;
     return k;
+}
+
+// Status fields are written by other blocks between the phases of the persistent kernel:
+// read them through the memory system, never from a register copy.
+template <typename T>
+__device__ __forceinline__ T vload(const T &x) {
+    return *(const volatile T *)&x;
 }
 
 // Alive-adjacency set of p if p has one (high degree), else null.
@@ -251,10 +268,9 @@ __device__ __forceinline__ UnitInfo unit_info(const LossArgs &a, int u) {
 // Splits the frontier's edge sides into detection items of at most 32 pairs (one warp
 // each), so a hub row is spread over many warps.  Sides that do not fit the item list are
 // left to the next slot of the round (resume point).
-__global__ void k_pair_items(LossArgs a) {
+__device__ void ph_pair_items(const LossArgs &a) {
     DevStatus *st = a.st;
-    if (st->alive == 0) return;
-    const int units = 2 * st->nF, u0 = st->unit_begin;
+    const int units = 2 * vload(st->nF), u0 = vload(st->unit_begin);
     const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * blockDim.x;
     for (int b = u0 + blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < units; b += stride) {
@@ -286,23 +302,23 @@ __global__ void k_pair_items(LossArgs a) {
 // Loss detection, one warp per item: lane i tests the pair of slot item.y + i.  A pair is
 // kept if its endpoints are adjacent or (h = 2) share an alive neighbour; lanes whose test
 // needs a long row scan hand it to the whole warp, one pair after the other.
-__global__ void __launch_bounds__(kBlock) k_loss_detect(LossArgs a) {
+__device__ void ph_detect(const LossArgs &a) {
     __shared__ unsigned long long s_pairs, s_reads;
     DevStatus *st = a.st;
-    if (st->alive == 0) return;
     if (threadIdx.x == 0) {
         s_pairs = 0ull;
         s_reads = 0ull;
     }
     __syncthreads();
-    const int nitems = min(st->npitems, a.pitems_cap), round = st->round;
+    const int nitems = min(vload(st->npitems), a.pitems_cap), round = vload(st->round);
     const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     unsigned long long pairs = 0ull, reads_total = 0ull;
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nwarps) {
         const int2 item = a.pitems[it];
         const int u = item.x;
-        if (u < 0) continue;
+        // sides past an overflow are redone by the next slot of the round: skip them now
+        if (u < 0 || u > *(volatile int *)&st->overflow_unit) continue;
         const UnitInfo r = unit_info(a, u);
         const int sl = item.y + lane;
         int z = -1;
@@ -358,10 +374,9 @@ __global__ void __launch_bounds__(kBlock) k_loss_detect(LossArgs a) {
 // Splits every directed loss (v loses w) into update items of at most 32 of v's slots.
 // The detection reserved the work, so the item list always has room.  Also counts, once
 // per round and vertex, the alive edges whose support the updates bring up to date.
-__global__ void k_loss_items(LossArgs a) {
+__device__ void ph_loss_items(const LossArgs &a) {
     DevStatus *st = a.st;
-    if (st->alive == 0) return;
-    const int nd = 2 * min(st->nlost, a.lost_max), round = st->round;
+    const int nd = 2 * min(vload(st->nlost), a.lost_max), round = vload(st->round);
     const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * blockDim.x;
     unsigned long long touched = 0ull;
@@ -400,16 +415,15 @@ __global__ void k_loss_items(LossArgs a) {
 // PASS 1 (after the clears) handles v > z and tests w in B_new(z).  Distance is symmetric,
 // so w in B(z) is tested as z in B(w): all lanes read the same ball, at increasing z.
 template <int PASS>
-__global__ void __launch_bounds__(kBlock) k_loss_delta(LossArgs a) {
+__device__ void ph_delta(const LossArgs &a) {
     __shared__ unsigned long long s_tests, s_bytes;
     DevStatus *st = a.st;
-    if (st->alive == 0) return;
     if (threadIdx.x == 0) {
         s_tests = 0ull;
         s_bytes = 0ull;
     }
     __syncthreads();
-    const int nitems = min(st->nuitems, a.uitems_cap);
+    const int nitems = min(vload(st->nuitems), a.uitems_cap);
     const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     unsigned long long tests = 0ull, bytes_total = 0ull;
@@ -451,10 +465,9 @@ __global__ void __launch_bounds__(kBlock) k_loss_delta(LossArgs a) {
 }
 
 // Clears every lost member from the stored balls and empties the hash slots.
-__global__ void k_loss_apply(LossArgs a) {
+__device__ void ph_apply(const LossArgs &a) {
     DevStatus *st = a.st;
-    if (st->alive == 0) return;
-    const int nlost = min(st->nlost, a.lost_max);
+    const int nlost = min(vload(st->nlost), a.lost_max);
     for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < 2 * nlost; d += gridDim.x * blockDim.x) {
         const int4 L = a.lost[d >> 1];
         if (L.x < 0) continue;
@@ -496,6 +509,93 @@ __global__ void k_loss_apply(LossArgs a) {
     if ((threadIdx.x & 31) == 0 && real) atomicAdd((unsigned long long *)&st->st_lost, real);
 }
 
+// Frontier selection and removal in one pass (incremental rounds): every alive edge with
+// h-support <= k-2 joins F and is removed at once (Algorithm 1, lines 7-10).
+__device__ void ph_select_remove(const LossArgs &a) {
+    DevStatus *st = a.st;
+    if (vload(st->cont)) return;  // a continued round keeps its (already removed) frontier
+    const int k = vload(st->k), round = vload(st->round), thr = k - 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); e0 < a.m; e0 += stride) {
+        const int64_t e = e0 + (threadIdx.x & 31);
+        const bool p = e < a.m && a.sup[e] <= thr;
+        warp_append(p, (int32_t)e, &st->nF, a.frontier_w);
+        if (p)
+            remove_edge((int)e, k, round, a.eu, a.ev, a.slot_lo, a.slot_hi, a.sup, a.truss,
+                        a.stamp_w, a.col_live_w, a.deg_alive_w, a.hub_slot, a.hub_bits_w, a.Wpad);
+    }
+}
+
+// One launch per phase (the rounds of a CUDA graph).
+__global__ void __launch_bounds__(kBlock) k_pair_items(LossArgs a) {
+    if (vload(a.st->alive) == 0) return;
+    ph_pair_items(a);
+}
+__global__ void __launch_bounds__(kBlock) k_loss_detect(LossArgs a) {
+    if (vload(a.st->alive) == 0) return;
+    ph_detect(a);
+}
+__global__ void __launch_bounds__(kBlock) k_loss_items(LossArgs a) {
+    if (vload(a.st->alive) == 0) return;
+    ph_loss_items(a);
+}
+template <int PASS>
+__global__ void __launch_bounds__(kBlock) k_loss_delta(LossArgs a) {
+    if (vload(a.st->alive) == 0) return;
+    ph_delta<PASS>(a);
+}
+__global__ void __launch_bounds__(kBlock) k_loss_apply(LossArgs a) {
+    if (vload(a.st->alive) == 0) return;
+    ph_apply(a);
+}
+
+constexpr int kPBlock = 512;  // threads per block of the persistent kernel
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Persistent round kernel (cooperative launch, every block resident): runs up to
+// `max_slots` round slots, each the eight phases of an incremental round separated by grid
+// barriers, and stops early once no edge is alive or an error is flagged.  Block 0 adds
+// the time of each phase to the status block.
+__global__ void __launch_bounds__(kPBlock, 3) k_rounds_persistent(LossArgs a, int max_slots) {
+    DevStatus *st = a.st;
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long t_prev = timer ? global_ns() : 0ull;
+    auto phase_done = [&](int p) -> bool {
+        if (!grid_barrier(st)) return false;
+        if (timer) {
+            const unsigned long long t = global_ns();
+            st->st_phase_ns[p] += t - t_prev;
+            t_prev = t;
+        }
+        return true;
+    };
+    for (int slot = 0; slot < max_slots; slot++) {
+        if (vload(st->alive) == 0 || vload(st->err) != 0) break;
+        ph_select_remove(a);
+        if (!phase_done(0)) return;
+        ph_pair_items(a);
+        if (!phase_done(1)) return;
+        ph_detect(a);
+        if (!phase_done(2)) return;
+        ph_loss_items(a);
+        if (!phase_done(3)) return;
+        ph_delta<0>(a);
+        if (!phase_done(4)) return;
+        ph_apply(a);
+        if (!phase_done(5)) return;
+        ph_delta<1>(a);
+        if (!phase_done(6)) return;
+        minreduce_body<kPBlock / 32>(a.sup, a.m, st, 0);
+        if (!phase_done(7)) return;
+        if (timer) st->st_slots++;
+    }
+}
+
 LossArgs loss_args(Handle *H) {
     PeelWork &w = H->w;
     GraphDev &g = H->g;
@@ -529,6 +629,15 @@ LossArgs loss_args(Handle *H) {
     a.hub_slot = w.hub_slot;
     a.hub_bits = w.hub_bits;
     a.Wpad = w.Wpad;
+    a.m = g.m;
+    a.slot_lo = g.slot_lo;
+    a.slot_hi = g.slot_hi;
+    a.truss = w.truss;
+    a.stamp_w = w.stamp;
+    a.frontier_w = w.frontier;
+    a.col_live_w = w.col_live;
+    a.deg_alive_w = w.deg_alive;
+    a.hub_bits_w = w.hub_bits;
     a.st = w.status;
     return a;
 }
@@ -537,6 +646,33 @@ LossArgs loss_args(Handle *H) {
 
 // Enqueues the loss detection and the support updates of one incremental round (after
 // k_remove, before the min reduction).  ev_mid (nullable) is recorded between the two.
+// Launches the persistent round kernel once (at most max_slots round slots).  The grid is
+// every block that can be resident at once, as a cooperative launch requires.
+htd_status launch_persistent_rounds(Handle *H, cudaStream_t s, int max_slots, int64_t *launches) {
+    LossArgs a = loss_args(H);
+    static thread_local int grid_cached = 0, dev_cached = -1;
+    if (grid_cached == 0 || dev_cached != H->g.device) {
+        int occ = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rounds_persistent,
+                                                                      kPBlock, 0);
+        if (e != cudaSuccess || occ < 1) {
+            set_last_error("persistent round kernel: no resident block fits");
+            return HTD_ECUDA;
+        }
+        grid_cached = H->num_sms * occ;
+        dev_cached = H->g.device;
+    }
+    void *args[] = {&a, &max_slots};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_rounds_persistent, dim3(grid_cached),
+                                                dim3(kPBlock), args, 0, s);
+    (*launches)++;
+    if (e != cudaSuccess) {
+        set_last_error(std::string("persistent round kernel: ") + cudaGetErrorString(e));
+        return HTD_ECUDA;
+    }
+    return HTD_OK;
+}
+
 htd_status enqueue_loss_kernels(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t ev_mid,
                                 unsigned record_flags) {
     LossArgs a = loss_args(H);

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "htd_internal.h"
+#include "htd_round.cuh"
 #include "htd_scan.cuh"
 
 namespace htd {
@@ -485,22 +486,9 @@ __global__ void k_remove(const int32_t *__restrict__ frontier, DevStatus *st,
                          uint32_t *__restrict__ hub_bits, int32_t Wpad) {
     if (st->alive == 0 || st->cont) return;  // a continued round removed its frontier already
     const int nF = st->nF, k = st->k, round = st->round;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
-        const int e = frontier[i];
-        const int u = eu[e], v = ev[e];
-        truss[e] = k;
-        stamp[e] = round;
-        sup[e] = INT_MAX;
-        col_live[slot_lo[e]] = ~v;
-        col_live[slot_hi[e]] = ~u;
-        atomicSub(&deg_alive[u], 1);
-        atomicSub(&deg_alive[v], 1);
-        if (hub_slot) {  // alive-adjacency sets of high-degree endpoints
-            const int hu = hub_slot[u], hv = hub_slot[v];
-            if (hu >= 0) atomicAnd(hub_bits + (int64_t)hu * Wpad + (v >> 5), ~(1u << (v & 31)));
-            if (hv >= 0) atomicAnd(hub_bits + (int64_t)hv * Wpad + (u >> 5), ~(1u << (u & 31)));
-        }
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x)
+        remove_edge(frontier[i], k, round, eu, ev, slot_lo, slot_hi, sup, truss, stamp, col_live,
+                    deg_alive, hub_slot, hub_bits, Wpad);
 }
 
 // Alive-adjacency n-bit sets of the high-degree vertices (all edges alive), block per hub.
@@ -521,97 +509,11 @@ __global__ void __launch_bounds__(kBlock) k_hub_init(const int32_t *__restrict__
     }
 }
 
-// Minimum alive h-support and alive count; the last block to finish closes the round:
-// bookkeeping, next level k = max(k, min + 2) (Algorithm 1's bins skip empty levels),
-// and reset of the per-round counters.
+// Minimum alive h-support and alive count; the last block to finish closes the round.
 __global__ void __launch_bounds__(kBlock) k_minreduce(const int32_t *__restrict__ sup, int64_t m,
-                                                      DevStatus *st, int32_t initial,
-                                                      const int32_t *__restrict__ edge_touch) {
-    __shared__ int32_t s_min[kNWarps];
-    __shared__ long long s_cnt[kNWarps];
-    __shared__ long long s_touch[kNWarps];
-    __shared__ bool s_last;
+                                                      DevStatus *st, int32_t initial) {
     if (!initial && st->alive == 0) return;
-    const int round = st->round;
-    // count touched edges once per round: in its last (finished) slot
-    const bool count_touch = edge_touch && st->overflow_unit == INT_MAX;
-    int lmin = INT_MAX;
-    long long lc = 0, lt = 0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int s = sup[e];
-        if (s != INT_MAX) {
-            lmin = min(lmin, s);
-            lc++;
-            if (count_touch && edge_touch[e] == round) lt++;
-        }
-    }
-    lmin = warp_min(lmin);
-    lc = warp_sum_ll(lc);
-    lt = warp_sum_ll(lt);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        s_min[wid] = lmin;
-        s_cnt[wid] = lc;
-        s_touch[wid] = lt;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int bm = INT_MAX;
-        long long bc = 0, bt = 0;
-        for (int j = 0; j < kNWarps; j++) {
-            bm = min(bm, s_min[j]);
-            bc += s_cnt[j];
-            bt += s_touch[j];
-        }
-        if (bm != INT_MAX) atomicMin(&st->min_acc, bm);
-        if (bc) atomicAdd((unsigned long long *)&st->alive_acc, (unsigned long long)bc);
-        if (bt) atomicAdd((unsigned long long *)&st->st_recomputed, (unsigned long long)bt);
-        __threadfence();
-        const unsigned ticket = atomicAdd(&st->done_blocks, 1u);
-        s_last = (ticket == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        const int mn = atomicAdd(&st->min_acc, 0);
-        const long long al = (long long)atomicAdd((unsigned long long *)&st->alive_acc, 0ull);
-        const int nF = st->nF;
-        // an incremental round whose lost pairs did not all fit continues in the next slot
-        const bool unfinished = !initial && st->overflow_unit != INT_MAX && al > 0;
-        st->cont = unfinished ? 1 : 0;
-        st->unit_begin = unfinished ? st->overflow_unit : 0;
-        st->overflow_unit = INT_MAX;
-        if (!initial && nF > 0 && !unfinished) {
-            if (st->k != st->last_k) {
-                st->levels++;
-                st->last_k = st->k;
-            }
-            st->max_k = max(st->max_k, st->k);
-            st->round++;
-            st->st_frontier += nF;
-            int cands = 0;
-            for (int j = 0; j < kMaxH; j++) cands += st->cand_cnt[j];
-            st->st_candidates += cands;
-            st->st_changed += st->nchanged;
-        }
-        st->alive = al;
-        if (al > 0 && !unfinished) st->k = max(st->k, mn + 2);
-        st->min_acc = INT_MAX;
-        st->alive_acc = 0;
-        st->done_blocks = 0u;
-        if (!unfinished) st->nF = 0;
-        for (int j = 0; j < kMaxH; j++) st->cand_cnt[j] = 0;
-        st->nchanged = 0;
-        st->nlost = 0;
-        st->npitems = 0;
-        st->nuitems = 0;
-        st->upd_work = 0;
-        st->nitems = 0;
-        st->q_ball = 0;
-        st->q_items = 0;
-        __threadfence();
-    }
+    minreduce_body<kNWarps>(sup, m, st, initial);
 }
 
 __global__ void k_init_deg(int32_t n, const int32_t *__restrict__ row_ptr,
@@ -795,7 +697,7 @@ htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) 
         // (sized with the graph: 2m adjacency slots)
         w.pitems_cap = std::min<int64_t>((int64_t)1 << 22, std::max<int64_t>(4096, 2 * m));
         // adjacency slots the updates of one batch may visit
-        w.upd_budget = std::min<int64_t>((int64_t)1 << 28, std::max<int64_t>(1 << 16, 64 * m));
+        w.upd_budget = std::min<int64_t>((int64_t)1 << 30, std::max<int64_t>(1 << 16, 256 * m));
         w.uitems_cap = 2 * w.lost_max + w.upd_budget / 32 + 1024;
         HTD_CHECK(alloc_n(&w.pitems, w.pitems_cap));
         HTD_CHECK(alloc_n(&w.uitems, w.uitems_cap));
@@ -917,7 +819,7 @@ htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
         (*launches)++;
         HTD_CHECK(cudaGetLastError());
     }
-    k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 1, nullptr);
+    k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 1);
     (*launches)++;
     HTD_CHECK(cudaGetLastError());
     if (timing) {
@@ -966,7 +868,7 @@ htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent
         if (ls != HTD_OK) return ls;
         mark(4);
         mark(5);
-        k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 0, nullptr);
+        k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 0);
         mark(6);
         (*launches)++;
         HTD_CHECK(cudaGetLastError());
@@ -992,7 +894,7 @@ htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent
     HsupArgs ha = hsup_args(H, 0);
     k_hsup<<<w.grid_hsup, kBlock, w.smem_hsup, s>>>(ha);
     mark(5);
-    k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 0, nullptr);
+    k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 0);
     mark(6);
     *launches += 4;
     HTD_CHECK(cudaGetLastError());

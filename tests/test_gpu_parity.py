@@ -135,7 +135,7 @@ def test_h_support_against_floyd_warshall(htd):
 
 # ---- a4-a7: peeling -----------------------------------------------------------------------------
 
-MODES = {"incremental": 0, "rebuild": 4}
+MODES = {"incremental": 0, "graph": 16, "rebuild": 4}
 
 
 @pytest.mark.parametrize("mode", sorted(MODES))
@@ -147,7 +147,7 @@ def test_truss_corpus(htd, oracle_mod, h, mode):
         t, _, st = htd.htd_truss_decompose(g, h, flags=MODES[mode])
         np.testing.assert_array_equal(host(t), og.truss_decompose(h)[0])
         if g.m:
-            assert st["incremental"] == (1 if (h <= 2 and mode == "incremental") else 0)
+            assert st["incremental"] == (1 if (h <= 2 and mode != "rebuild") else 0)
 
 
 @pytest.mark.parametrize("mode", sorted(MODES))
@@ -279,8 +279,11 @@ def test_incremental_matches_rebuild_on_hubby_graph(htd):
     for h in (1, 2):
         a, sa, st_a = htd.htd_truss_decompose(g, h, stamps=True)
         b, sb, st_b = htd.htd_truss_decompose(g, h, stamps=True, flags=htd.HTD_OPT_REBUILD)
-        assert st_a["incremental"] == 1 and st_b["incremental"] == 0
+        c, sc, st_c = htd.htd_truss_decompose(g, h, stamps=True, flags=htd.HTD_OPT_GRAPH_ROUNDS)
+        assert st_a["incremental"] == 1 and st_b["incremental"] == 0 and st_c["incremental"] == 1
+        assert st_a["round_kernel_launches"] >= 1 and st_c["round_kernel_launches"] == 0
         assert torch.equal(a, b) and torch.equal(sa, sb)
+        assert torch.equal(a, c) and torch.equal(sa, sc)
 
 
 @pytest.mark.parametrize("h", [1, 2])
@@ -292,6 +295,9 @@ def test_batched_rounds_match_oracle(htd, oracle_mod, h):
         og = oracle_mod.OracleGraph.from_raw(n, s, d)
         t, stamp, st = htd.htd_truss_decompose(g, h, stamps=True,
                                                flags=htd.HTD_OPT_TINY_LOSS_TABLE)
+        t2, stamp2, _ = htd.htd_truss_decompose(
+            g, h, stamps=True, flags=htd.HTD_OPT_TINY_LOSS_TABLE | htd.HTD_OPT_GRAPH_ROUNDS)
+        assert torch.equal(t, t2) and torch.equal(stamp, stamp2)
         t_ref, stamp_ref, rounds = og.truss_decompose(h)
         np.testing.assert_array_equal(host(t), t_ref)
         np.testing.assert_array_equal(host(stamp), stamp_ref)  # same rounds as the oracle
