@@ -244,21 +244,31 @@ def run_gpu(args, world, rank, local):
     def mean(key):
         return float(np.mean([s[key] for s in stats]))
 
-    rounds_timed = max(1, s0["timed_slots"])
+    slots = max(1, s0["slots"])
+    timed = max(1, s0["timed_slots"])
+    m_edges = float(m)
     # kernel classes of one step: (name, device ms per step, launches per step, alg bytes)
-    ball_store_bytes = mean("alg_bytes_ball") / 2 if s0["incremental"] else None
-    classes = [
-        ("k_ball (initial store)", mean("ms_initial_ball"), 1, ball_store_bytes),
-        ("k_hsup (initial)", mean("ms_initial_hsup"), 1,
-         mean("alg_bytes_hsup") if s0["incremental"] else None),
-        ("k_loss_detect", mean("ms_find"), rounds_timed,
-         mean("alg_bytes_detect") if s0["incremental"] else None),
-        ("k_loss_delta + k_loss_apply", mean("ms_update"), 3 * rounds_timed,
-         mean("alg_bytes_update") if s0["incremental"] else None),
+    if s0["round_kernel_launches"] > 0:  # persistent round kernel
+        scan = 8.0 * m_edges * slots  # two passes over the supports per slot
+        classes = [("k_rounds_persistent", mean("ms_round_kernel"), s0["round_kernel_launches"],
+                     mean("alg_bytes_detect") + mean("alg_bytes_update") + scan)]
+    elif s0["incremental"]:
+        # phase times are sampled (every 8th batch); scale the per-slot mean to all slots
+        per = slots / timed
+        classes = [
+            ("k_loss_detect", mean("ms_find") * per, slots, mean("alg_bytes_detect")),
+            ("k_loss_delta", mean("ms_update") * per, slots, mean("alg_bytes_update")),
+            ("k_inc_select", mean("ms_select") * per, slots, 4.0 * m_edges * slots),
+            ("k_loss_apply_reduce", mean("ms_minreduce") * per, slots, 4.0 * m_edges * slots),
+        ]
+    else:
+        per = slots / timed
+        classes = [("k_ball (rebuild rounds)", mean("ms_ball") * per, slots, None),
+                   ("k_hsup (rounds)", mean("ms_update") * per, slots, None)]
+    classes += [
+        ("k_ball (initial store)", mean("ms_initial_ball"), 1, mean("alg_bytes_ball") / 2),
+        ("k_hsup (initial)", mean("ms_initial_hsup"), 1, mean("alg_bytes_hsup")),
     ]
-    if not s0["incremental"]:
-        classes = [("k_ball (rebuild rounds)", mean("ms_ball"), rounds_timed, None),
-                   ("k_hsup (rounds)", mean("ms_update"), rounds_timed, None)]
     kern, k_ms, k_launches, k_bytes = max(classes, key=lambda c: c[1])
     achieved = (k_bytes / (k_ms / 1e3)) / 1e9 if (k_bytes and k_ms > 0) else None
     traffic = None
@@ -273,9 +283,6 @@ def run_gpu(args, world, rank, local):
         except (OSError, ValueError):
             traffic = None
     phases = {name: {"ms": ms, "launches": ln, "alg_bytes": b} for name, ms, ln, b in classes}
-    phases["select"] = {"ms": mean("ms_select"), "launches": rounds_timed}
-    phases["remove"] = {"ms": mean("ms_remove"), "launches": rounds_timed}
-    phases["minreduce"] = {"ms": mean("ms_minreduce"), "launches": rounds_timed}
     hsup_rate = float(np.mean([s["hsup_evals"] for s in stats])) / (ms_step / 1e3)
     cpu = None
     if not args.no_cpu_baseline and world == 1:

@@ -73,8 +73,8 @@ typedef struct htd_stats {
     int64_t member_tests;    /* incremental rounds: ball-membership tests of support updates */
     int64_t kernel_launches; /* kernels this library launched for the call */
     int64_t ball_pool_bytes; /* device bytes held by the h-hop balls */
-    int64_t timed_slots;     /* round slots timed (a slot runs one round or one batch of a
-                                continued round; slots after the last round are no-ops) */
+    int64_t timed_slots;     /* round slots whose phases were timed (with HTD_OPT_TIMING the
+                                graph path times every 8th batch of 16 slots) */
     double alg_bytes_ball;   /* algorithmic bytes: ball builds (initial and rebuilds) */
     double alg_bytes_hsup;   /* algorithmic bytes: full h-support intersections */
     double alg_bytes_detect; /* algorithmic bytes: loss detection (incremental rounds) */
@@ -93,6 +93,7 @@ typedef struct htd_stats {
     int32_t round_kernel_launches;
     int32_t incremental;     /* 1 if the rounds used incremental support updates */
     int32_t reserved;
+    int64_t slots;           /* round slots that ran (rounds plus continued batches) */
 } htd_stats;
 
 /* Option flags for htd_truss_decompose_ex. */
@@ -100,8 +101,9 @@ typedef struct htd_stats {
 #define HTD_OPT_NO_GRAPH 2u  /* launch each peel round directly instead of via a CUDA graph */
 #define HTD_OPT_REBUILD 4u   /* h <= 2: rebuild shrunk balls and recompute their edges' support
                                 instead of the incremental lost-pair updates (same results) */
-#define HTD_OPT_GRAPH_ROUNDS 16u   /* h <= 2: one launch per phase in a CUDA graph of 16 rounds,
-                                       instead of the persistent round kernel (same results) */
+#define HTD_OPT_PERSISTENT_ROUNDS 16u  /* h <= 2: all rounds in a persistent cooperative
+                                          kernel (phases split by grid barriers) instead of
+                                          a CUDA graph of 16 rounds (same results) */
 #define HTD_OPT_TINY_LOSS_TABLE 8u  /* h <= 2: 128-slot lost-pair table, so that rounds run in
                                        many batches (a test of that path; slow) */
 

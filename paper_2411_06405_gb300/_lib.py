@@ -23,7 +23,7 @@ HTD_OPT_TIMING = 1
 HTD_OPT_NO_GRAPH = 2
 HTD_OPT_REBUILD = 4
 HTD_OPT_TINY_LOSS_TABLE = 8
-HTD_OPT_GRAPH_ROUNDS = 16
+HTD_OPT_PERSISTENT_ROUNDS = 16
 
 # every symbol include/htruss.h declares
 EXPORTED = (
@@ -66,6 +66,7 @@ class HtdStats(ctypes.Structure):
         ("round_kernel_launches", ctypes.c_int32),
         ("incremental", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+        ("slots", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -3,6 +3,7 @@
 // Every call runs on a stream private to the handle (a CUDA graph can be captured on it)
 // and is ordered against the caller's stream with two events: the private stream waits
 // for the caller's prior work, and the caller's stream waits for the call's work.
+#include <algorithm>
 #include <climits>
 #include <cstring>
 #include <string>
@@ -62,7 +63,9 @@ htd_status end_call(Handle *H, cudaStream_t user) {
 
 void destroy_graph(Handle *H) {
     if (H->graph_exec) cudaGraphExecDestroy(H->graph_exec);
+    if (H->graph_exec_timed) cudaGraphExecDestroy(H->graph_exec_timed);
     H->graph_exec = nullptr;
+    H->graph_exec_timed = nullptr;
     H->graph_h = 0;
     H->graph_rounds = 0;
 }
@@ -110,6 +113,8 @@ void htd_graph_free(htd_graph *g) {
     destroy_graph(H);
     htd::free_work(&H->w);
     htd::free_graph_dev(&H->g);
+    for (cudaEvent_t e : H->round_events) cudaEventDestroy(e);
+    H->round_events.clear();
     if (H->ev_in) cudaEventDestroy(H->ev_in);
     if (H->ev_out) cudaEventDestroy(H->ev_out);
     if (H->pstream) cudaStreamDestroy(H->pstream);
@@ -292,17 +297,8 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
     API_CHECK(cudaStreamSynchronize(H->pstream));
     API_TRY(check_status_err(w.status_host));
 
-    std::vector<cudaEvent_t> evs;
-    auto cleanup_events = [&]() {
-        for (cudaEvent_t e : evs) cudaEventDestroy(e);
-        evs.clear();
-    };
-    if (timing) {
-        evs.resize(htd::kRoundEvents * R, nullptr);
-        for (auto &e : evs) API_CHECK(cudaEventCreate(&e));
-    }
-    const int per_round = incremental ? 9 : h + 6;
-    const bool persistent = incremental && (flags & HTD_OPT_GRAPH_ROUNDS) == 0;
+    const int per_round = incremental ? 4 : h + 6;
+    const bool persistent = incremental && (flags & HTD_OPT_PERSISTENT_ROUNDS) != 0;
     if (persistent && w.status_host->alive > 0) {
         // one cooperative launch runs up to kPersistentSlots round slots; the host checks the
         // status block between launches
@@ -347,51 +343,56 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
         }
         cudaEventDestroy(p0);
         cudaEventDestroy(p1);
-        if (ps != HTD_OK) {
-            cleanup_events();
-            return ps;
-        }
+        if (ps != HTD_OK) return ps;
         const htd::DevStatus *sh = w.status_host;
         local.ms_select = sh->st_phase_ns[0] * 1e-6f;
-        local.ms_find = (sh->st_phase_ns[1] + sh->st_phase_ns[2]) * 1e-6f;
-        local.ms_update = (sh->st_phase_ns[3] + sh->st_phase_ns[4] + sh->st_phase_ns[5] +
-                           sh->st_phase_ns[6]) * 1e-6f;
-        local.ms_minreduce = sh->st_phase_ns[7] * 1e-6f;
+        local.ms_find = sh->st_phase_ns[1] * 1e-6f;
+        local.ms_update = sh->st_phase_ns[2] * 1e-6f;
+        local.ms_minreduce = sh->st_phase_ns[3] * 1e-6f;
         local.timed_slots = sh->st_slots;
     } else if (w.status_host->alive > 0) {
-        if (use_graph && (!H->graph_exec || H->graph_h != h || H->graph_rounds != (timing ? -R : R) ||
-                          H->graph_incremental != incremental)) {
-            destroy_graph(H);
+        // Graph path: R rounds per graph launch.  With HTD_OPT_TIMING a second graph with an
+        // external event record at every phase boundary runs every kTimedEvery-th batch (the
+        // events would otherwise slow every round); per-launch averages come from those.
+        constexpr int kTimedEvery = 8;
+        if (timing && H->round_events.empty()) {
+            H->round_events.resize(htd::kRoundEvents * R, nullptr);
+            for (auto &e : H->round_events) API_CHECK(cudaEventCreate(&e));
+        }
+        auto capture = [&](cudaGraphExec_t *exec, cudaEvent_t *ev) -> htd_status {
             cudaGraph_t graph = nullptr;
             API_CHECK(cudaStreamBeginCapture(H->pstream, cudaStreamCaptureModeThreadLocal));
             int64_t dummy = 0;
             htd_status cs = HTD_OK;
             for (int r = 0; r < R && cs == HTD_OK; r++)
-                cs = htd::enqueue_round(H, H->pstream, &dummy, timing ? &evs[htd::kRoundEvents * r] : nullptr);
+                cs = htd::enqueue_round(H, H->pstream, &dummy, ev ? ev + htd::kRoundEvents * r : nullptr);
             cudaError_t ce = cudaStreamEndCapture(H->pstream, &graph);
             if (cs != HTD_OK) {
                 if (graph) cudaGraphDestroy(graph);
-                cleanup_events();
                 return cs;
             }
             if (ce != cudaSuccess) {
-                cleanup_events();
                 set_last_error(std::string("htd: graph capture: ") + cudaGetErrorString(ce));
                 return HTD_ECUDA;
             }
-            ce = cudaGraphInstantiate(&H->graph_exec, graph, 0);
+            ce = cudaGraphInstantiate(exec, graph, 0);
             cudaGraphDestroy(graph);
             if (ce != cudaSuccess) {
-                H->graph_exec = nullptr;
-                cleanup_events();
+                *exec = nullptr;
                 set_last_error(std::string("htd: graph instantiate: ") + cudaGetErrorString(ce));
                 return HTD_ECUDA;
             }
+            return HTD_OK;
+        };
+        if (use_graph && (!H->graph_exec || H->graph_h != h || H->graph_incremental != incremental)) {
+            destroy_graph(H);
+            API_TRY(capture(&H->graph_exec, nullptr));
             H->graph_h = h;
-            H->graph_rounds = timing ? -R : R;
+            H->graph_rounds = R;
             H->graph_incremental = incremental;
         }
-        // timed graphs hold this call's events: recapture next time
+        if (use_graph && timing && !H->graph_exec_timed)
+            API_TRY(capture(&H->graph_exec_timed, H->round_events.data()));
         // every active round removes at least one edge, so m/R + 2 batches always suffice
         const int64_t round_cap = H->g.m + 2 * R + 2;
         // continued incremental rounds handle at least one new lost pair per slot, and a
@@ -402,40 +403,35 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
         bool timing_ok = timing;
         while (w.status_host->alive > 0) {
             if (++batches > batch_cap) {
-                cleanup_events();
                 set_last_error("htd_truss_decompose: no progress within the batch cap");
                 return HTD_ETIMEOUT;
             }
+            const bool timed = timing_ok && (batches % kTimedEvery == 1);
+            const int64_t slots_before = w.status_host->st_slots;
             if (use_graph) {
-                API_CHECK(cudaGraphLaunch(H->graph_exec, H->pstream));
+                API_CHECK(cudaGraphLaunch(timed ? H->graph_exec_timed : H->graph_exec, H->pstream));
                 launches += (int64_t)R * per_round;
             } else {
                 for (int r = 0; r < R; r++) {
-                    htd_status rs = htd::enqueue_round(
-                        H, H->pstream, &launches, timing ? &evs[htd::kRoundEvents * r] : nullptr);
-                    if (rs != HTD_OK) {
-                        cleanup_events();
-                        return rs;
-                    }
+                    API_TRY(htd::enqueue_round(H, H->pstream, &launches,
+                                               timed ? &H->round_events[htd::kRoundEvents * r] : nullptr));
                 }
             }
             count_launches();
             API_CHECK(cudaMemcpyAsync(w.status_host, w.status, sizeof(htd::DevStatus),
                                       cudaMemcpyDeviceToHost, H->pstream));
             API_CHECK(cudaStreamSynchronize(H->pstream));
-            htd_status es = check_status_err(w.status_host);
-            if (es != HTD_OK) {
-                cleanup_events();
-                return es;
-            }
-            if (timing_ok) {
-                // every slot of the batch ran (continued rounds and the no-op slots after the
-                // last round included), so all of them are timed
-                for (int r = 0; r < R && timing_ok; r++) {
+            API_TRY(check_status_err(w.status_host));
+            if (timed) {
+                // only the slots that ran a round (or a batch of one) count; those after the
+                // last round are no-ops
+                const int64_t active = std::min<int64_t>(R, w.status_host->st_slots - slots_before);
+                for (int r = 0; r < active && timing_ok; r++) {
                     float t[htd::kRoundEvents - 1];
                     for (int q = 0; q + 1 < htd::kRoundEvents; q++) {
-                        if (cudaEventElapsedTime(&t[q], evs[htd::kRoundEvents * r + q],
-                                                 evs[htd::kRoundEvents * r + q + 1]) != cudaSuccess) {
+                        if (cudaEventElapsedTime(&t[q], H->round_events[htd::kRoundEvents * r + q],
+                                                 H->round_events[htd::kRoundEvents * r + q + 1]) !=
+                            cudaSuccess) {
                             (void)cudaGetLastError();  // not sticky: report "no timing" instead
                             timing_ok = false;
                             break;
@@ -459,14 +455,11 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
                 if (!timing_ok) local.timed_slots = -1;
             }
             if (w.status_host->round > round_cap) {
-                cleanup_events();
                 set_last_error("htd_truss_decompose: round cap exceeded");
                 return HTD_ETIMEOUT;
             }
         }
-        if (timing) destroy_graph(H);
     }
-    cleanup_events();
     const int64_t m = H->g.m;
     if (m > 0) {
         API_CHECK(cudaMemcpyAsync(truss_dev, w.truss, m * 4, cudaMemcpyDeviceToDevice, H->pstream));
@@ -484,6 +477,7 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
         local.pairs_lost = s->st_lost;
         local.member_tests = s->st_tests;
         local.incremental = incremental ? 1 : 0;
+        local.slots = s->st_slots;
         local.levels = s->levels;
         local.ball_builds = H->g.n + s->st_candidates;
         local.balls_changed = s->st_changed;

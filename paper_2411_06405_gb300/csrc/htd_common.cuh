@@ -47,8 +47,9 @@ struct DevStatus {
     int32_t nuitems;           // support update items of the current batch
     int32_t pad1;
     long long upd_work;        // adjacency slots reserved for the batch's updates
-    unsigned bar_count;        // grid barrier of the persistent round kernel
-    unsigned bar_gen;
+    unsigned bar_count;        // grid barrier of the persistent round kernel: groups arrived
+    unsigned bar_gen;          // generation, advanced by the last arrival
+    unsigned bar_group[64];    // blocks arrived, per group of 32 blocks
     long long st_slots;        // round slots run by the persistent kernel
     unsigned long long st_phase_ns[8];  // persistent kernel: time per phase (block 0's view)
     int64_t st_ball_total;     // sum of the initial ball sizes

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -61,9 +62,9 @@ struct PeelWork {
     uint32_t *hub_bits = nullptr;  // nhub x Wpad words: alive neighbours as n-bit sets
     int32_t nhub = 0;
     int32_t hub_min_deg = 0;
-    int2 *pitems = nullptr;        // loss detection items: (edge side, first slot), <= 32 pairs
+    int4 *pitems = nullptr;        // loss detection items (edge side, first slot, x, y), <= 32 pairs
     int64_t pitems_cap = 0;
-    int2 *uitems = nullptr;        // support update items: (directed loss, first slot), <= 32
+    int4 *uitems = nullptr;        // support update items (first slot, v, w, row end), <= 32 slots
     int64_t uitems_cap = 0;
     int64_t upd_budget = 0;        // adjacency slots one batch of updates may visit
     int32_t *bfs_lists = nullptr;  // per-block BFS level lists (h >= 3)
@@ -83,7 +84,9 @@ struct Handle {
     PeelWork w;
     cudaStream_t pstream = nullptr;       // private stream (graph capture needs one)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    cudaGraphExec_t graph_exec = nullptr; // cached round graph
+    cudaGraphExec_t graph_exec = nullptr;       // cached round graph
+    cudaGraphExec_t graph_exec_timed = nullptr; // the same with an event at every phase
+    std::vector<cudaEvent_t> round_events;      // events of the timed graph
     int graph_h = 0;
     int graph_rounds = 0;
     bool graph_incremental = false;
@@ -109,8 +112,8 @@ htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent
 // Persistent kernel running up to max_slots incremental round slots (htd_loss.cu).
 htd_status launch_persistent_rounds(Handle *H, cudaStream_t s, int max_slots, int64_t *launches);
 
-// Incremental support updates of one round, h <= 2 (htd_loss.cu).
-htd_status enqueue_loss_kernels(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t ev_mid,
-                                unsigned record_flags);
+// One incremental round (h <= 2) as four launches, the graph path (htd_loss.cu).
+htd_status enqueue_incremental_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t *evs,
+                                     unsigned record_flags);
 
 }  // namespace htd

@@ -22,6 +22,7 @@
 // that batch), and a pair whose stored bit is already clear was handled by an earlier
 // batch of the same round, so it is skipped.  Detection records the first frontier edge
 // side it could not finish; the next round slot resumes there without selecting anew.
+#include <algorithm>
 #include <cstdint>
 
 #include "htd_internal.h"
@@ -68,9 +69,9 @@ struct LossArgs {
     const uint32_t *hub_bits;
     int32_t Wpad;
     int32_t pitems_cap;
-    int2 *pitems;
+    int4 *pitems;
     int32_t uitems_cap;
-    int2 *uitems;
+    int4 *uitems;
     long long upd_budget;
     DevStatus *st;
 };
@@ -134,7 +135,7 @@ __device__ __forceinline__ bool alive_adjacent(const LossArgs &a, int p, int q, 
 }
 
 // Short rows are scanned by one lane; pairs whose shorter row is longer go to the warp.
-constexpr int kInlineScan = 4;
+constexpr int kInlineScan = 8;
 
 enum PairState { kKept = 0, kLost = 1, kHard = 2 };
 
@@ -155,11 +156,18 @@ __device__ __forceinline__ int pair_quick(const LossArgs &a, int &p, int &q, uns
     if (a.h < 2) return kLost;
     // with q's set every scanned neighbour costs one read; without it, a binary search
     if (min(dp, dq) > (qset ? 8 * kInlineScan : kInlineScan)) return kHard;
-    const int re = a.row_ptr[p + 1];
-    for (int s = a.row_ptr[p]; s < re; s++) {
-        const int y = a.col_live[s];
-        reads++;
-        if (y >= 0 && alive_adjacent_set(a, qset, q, y, reads)) return kKept;
+    const int rb = a.row_ptr[p], re = a.row_ptr[p + 1];
+    // four slots at a time: their loads (and their set lookups) are independent
+    for (int s0 = rb; s0 < re; s0 += 4) {
+        int y[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) y[j] = (s0 + j < re) ? a.col_live[s0 + j] : -1;
+        bool hit = false;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (y[j] >= 0) hit |= alive_adjacent_set(a, qset, q, y[j], reads);
+        reads += (unsigned)min(4, re - s0);
+        if (hit) return kKept;
     }
     return kLost;
 }
@@ -171,13 +179,20 @@ __device__ __forceinline__ bool warp_common_neighbour(const LossArgs &a, int p, 
     const int lane = threadIdx.x & 31;
     const int rb = a.row_ptr[p], re = a.row_ptr[p + 1];
     const uint32_t *qset = hub_set(a, q, reads);
-    for (int s0 = rb; s0 < re; s0 += 32) {
-        const int s = s0 + lane;
+    for (int s0 = rb; s0 < re; s0 += 128) {
+        int y[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int s = s0 + 32 * j + lane;
+            y[j] = (s < re) ? a.col_live[s] : -1;
+        }
         bool hit = false;
-        if (s < re) {
-            const int y = a.col_live[s];
-            reads++;
-            hit = (y >= 0) && alive_adjacent_set(a, qset, q, y, reads);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (y[j] >= 0) {
+                reads++;
+                hit |= alive_adjacent_set(a, qset, q, y[j], reads);
+            }
         }
         if (__any_sync(0xffffffffu, hit)) return true;
     }
@@ -218,9 +233,9 @@ __device__ __forceinline__ bool ball_contains(const LossArgs &a, int z, int w, u
 // record and the pair's update work (both rows are visited by the support updates) are
 // reserved against the batch limits; a pair that does not fit marks its edge side u as
 // the point where the next slot of this round resumes.
-__device__ __forceinline__ void record_lost(const LossArgs &a, DevStatus *st, int x, int z, int u,
-                                            unsigned &reads) {
-    if (!ball_contains(a, x, z, reads)) return;  // stored bit already clear
+__device__ __forceinline__ int record_lost(const LossArgs &a, DevStatus *st, int x, int z, int u,
+                                           unsigned &reads) {
+    if (!ball_contains(a, x, z, reads)) return -1;  // stored bit already clear
     const long long work = (long long)(a.row_ptr[x + 1] - a.row_ptr[x]) +
                            (a.row_ptr[z + 1] - a.row_ptr[z]);
     const long long before =
@@ -229,7 +244,7 @@ __device__ __forceinline__ void record_lost(const LossArgs &a, DevStatus *st, in
     if (idx >= a.lost_max || before + work > a.upd_budget) {
         atomicMin(&st->overflow_unit, u);
         if (idx < a.lost_max) a.lost[idx] = make_int4(-1, -1, -1, 0);
-        return;
+        return -1;
     }
     const unsigned long long key = pair_key(x, z);
     unsigned long long slot = mix64(key) & a.cap_mask;
@@ -244,6 +259,64 @@ __device__ __forceinline__ void record_lost(const LossArgs &a, DevStatus *st, in
         slot = (slot + 1) & a.cap_mask;
     }
     a.lost[idx] = rec;
+    return rec.x >= 0 ? idx : -1;
+}
+
+// Is the pair {p,q} among this batch's lost pairs?
+__device__ __forceinline__ bool lost_now(const LossArgs &a, int p, int q, unsigned &bytes) {
+    const unsigned long long key = pair_key(p, q);
+    unsigned long long slot = mix64(key) & a.cap_mask;
+    for (unsigned long long probe = 0; probe <= a.cap_mask; probe++) {
+        const unsigned long long k = a.keys[slot];
+        bytes += 8;
+        if (k == key) return true;
+        if (k == kEmpty) return false;
+        slot = (slot + 1) & a.cap_mask;
+    }
+    return false;
+}
+
+// Update items of the new lost pairs of a warp, one pair per lane (rec >= 0): direction 0
+// = v0 = min loses v1, in runs of 32 of v0's slots; direction 1 = v1 loses v0.  Each lane
+// reserves and writes its own items when they are few; long rows are written by the whole
+// warp, one pair after the other.  Also counts, once per round and vertex, the alive edges
+// whose support the updates bring up to date.
+__device__ __forceinline__ void emit_update_items(const LossArgs &a, DevStatus *st, int rec, int x,
+                                                  int z, int round, unsigned long long &touched) {
+    constexpr int kOwnItems = 8;
+    const int lane = threadIdx.x & 31;
+    int v0 = 0, v1 = 0, rb0 = 0, re0 = 0, rb1 = 0, re1 = 0, n0 = 0, n1 = 0, base = 0;
+    if (rec >= 0) {
+        v0 = min(x, z);
+        v1 = max(x, z);
+        rb0 = a.row_ptr[v0];
+        re0 = a.row_ptr[v0 + 1];
+        rb1 = a.row_ptr[v1];
+        re1 = a.row_ptr[v1 + 1];
+        n0 = (re0 - rb0 + 31) >> 5;
+        n1 = (re1 - rb1 + 31) >> 5;
+        base = atomicAdd(&st->nuitems, n0 + n1);
+        if (atomicExch(a.vtouch + v0, round) != round) touched += a.deg_alive[v0];
+        if (atomicExch(a.vtouch + v1, round) != round) touched += a.deg_alive[v1];
+        if (n0 + n1 <= kOwnItems) {
+            for (int c = 0; c < n0 + n1 && base + c < a.uitems_cap; c++)
+                a.uitems[base + c] = (c < n0) ? make_int4(rb0 + 32 * c, v0, v1, re0)
+                                              : make_int4(rb1 + 32 * (c - n0), v1, v0, re1);
+        }
+    }
+    unsigned big = __ballot_sync(0xffffffffu, rec >= 0 && n0 + n1 > kOwnItems);
+    while (big) {
+        const int l = __ffs(big) - 1;
+        big &= big - 1;
+        const int b = __shfl_sync(0xffffffffu, base, l);
+        const int c0 = __shfl_sync(0xffffffffu, n0, l), c1 = __shfl_sync(0xffffffffu, n1, l);
+        const int w0 = __shfl_sync(0xffffffffu, v0, l), w1 = __shfl_sync(0xffffffffu, v1, l);
+        const int b0 = __shfl_sync(0xffffffffu, rb0, l), e0 = __shfl_sync(0xffffffffu, re0, l);
+        const int b1 = __shfl_sync(0xffffffffu, rb1, l), e1 = __shfl_sync(0xffffffffu, re1, l);
+        for (int c = lane; c < c0 + c1 && b + c < a.uitems_cap; c += 32)
+            a.uitems[b + c] = (c < c0) ? make_int4(b0 + 32 * c, w0, w1, e0)
+                                       : make_int4(b1 + 32 * (c - c0), w1, w0, e1);
+    }
 }
 
 // Pair enumeration of edge side u = (edge F[u/2], side u%2): side 0 of (a,b) pairs a with
@@ -275,10 +348,12 @@ __device__ void ph_pair_items(const LossArgs &a) {
     const int stride = gridDim.x * blockDim.x;
     for (int b = u0 + blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < units; b += stride) {
         const int u = b + lane;
-        int nch = 0, start = 0;
+        int nch = 0, start = 0, x = 0, y = 0;
         if (u < units) {
             const UnitInfo r = unit_info(a, u);
             start = r.start;
+            x = r.x;
+            y = r.y;
             nch = (r.stop - r.start + 31) >> 5;
         }
         int incl = nch;
@@ -294,8 +369,18 @@ __device__ void ph_pair_items(const LossArgs &a) {
         const int first = base + incl - nch;
         const bool fits = first + nch <= a.pitems_cap;
         if (!fits && nch) atomicMin(&st->overflow_unit, u);
-        for (int c = 0; c < nch && first + c < a.pitems_cap; c++)
-            a.pitems[first + c] = fits ? make_int2(u, start + 32 * c) : make_int2(-1, 0);
+        // the whole warp writes each lane's items in turn (a hub row has hundreds)
+        unsigned todo = __ballot_sync(0xffffffffu, nch > 0);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int f = __shfl_sync(0xffffffffu, first, l), c_n = __shfl_sync(0xffffffffu, nch, l);
+            const int ul = __shfl_sync(0xffffffffu, u, l), sl = __shfl_sync(0xffffffffu, start, l);
+            const int xl = __shfl_sync(0xffffffffu, x, l), yl = __shfl_sync(0xffffffffu, y, l);
+            const bool fl = __shfl_sync(0xffffffffu, fits, l);
+            for (int c = lane; c < c_n && f + c < a.pitems_cap; c += 32)
+                a.pitems[f + c] = fl ? make_int4(ul, sl + 32 * c, xl, yl) : make_int4(-1, 0, 0, 0);
+        }
     }
 }
 
@@ -305,6 +390,7 @@ __device__ void ph_pair_items(const LossArgs &a) {
 __device__ void ph_detect(const LossArgs &a) {
     __shared__ unsigned long long s_pairs, s_reads;
     DevStatus *st = a.st;
+    unsigned long long touched = 0ull;
     if (threadIdx.x == 0) {
         s_pairs = 0ull;
         s_reads = 0ull;
@@ -312,14 +398,18 @@ __device__ void ph_detect(const LossArgs &a) {
     __syncthreads();
     const int nitems = min(vload(st->npitems), a.pitems_cap), round = vload(st->round);
     const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
     unsigned long long pairs = 0ull, reads_total = 0ull;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nwarps) {
-        const int2 item = a.pitems[it];
+        const int4 item = a.pitems[it];
         const int u = item.x;
         // sides past an overflow are redone by the next slot of the round: skip them now
         if (u < 0 || u > *(volatile int *)&st->overflow_unit) continue;
-        const UnitInfo r = unit_info(a, u);
+        UnitInfo r;
+        r.x = item.z;
+        r.y = item.w;
+        r.rb = a.row_ptr[r.y];
+        r.stop = (a.h < 2) ? r.rb : a.row_ptr[r.y + 1];
         const int sl = item.y + lane;
         int z = -1;
         unsigned reads = 0;
@@ -353,13 +443,16 @@ __device__ void ph_detect(const LossArgs &a) {
             const bool kept = warp_common_neighbour(a, hp, hq, reads);
             if (lane == leader) state = kept ? kKept : kLost;
         }
-        if (state == kLost) record_lost(a, st, r.x, z, u, reads);
+        const int rec = (state == kLost) ? record_lost(a, st, r.x, z, u, reads) : -1;
+        emit_update_items(a, st, rec, r.x, z, round, touched);
         reads_total += reads;
     }
     for (int o = 16; o > 0; o >>= 1) {
         pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
         reads_total += __shfl_xor_sync(0xffffffffu, reads_total, o);
+        touched += __shfl_xor_sync(0xffffffffu, touched, o);
     }
+    if (lane == 0 && touched) atomicAdd((unsigned long long *)&st->st_recomputed, touched);
     if (lane == 0 && pairs) {
         atomicAdd(&s_pairs, pairs);
         atomicAdd(&s_reads, reads_total);
@@ -371,50 +464,12 @@ __device__ void ph_detect(const LossArgs &a) {
     }
 }
 
-// Splits every directed loss (v loses w) into update items of at most 32 of v's slots.
-// The detection reserved the work, so the item list always has room.  Also counts, once
-// per round and vertex, the alive edges whose support the updates bring up to date.
-__device__ void ph_loss_items(const LossArgs &a) {
-    DevStatus *st = a.st;
-    const int nd = 2 * min(vload(st->nlost), a.lost_max), round = vload(st->round);
-    const int lane = threadIdx.x & 31;
-    const int stride = gridDim.x * blockDim.x;
-    unsigned long long touched = 0ull;
-    for (int b = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < nd; b += stride) {
-        const int d = b + lane;
-        int nch = 0, rb = 0;
-        if (d < nd) {
-            const int4 L = a.lost[d >> 1];
-            if (L.x >= 0) {
-                const int v = (d & 1) ? L.y : L.x;
-                rb = a.row_ptr[v];
-                nch = (a.row_ptr[v + 1] - rb + 31) >> 5;
-                if (atomicExch(a.vtouch + v, round) != round) touched += a.deg_alive[v];
-            }
-        }
-        int incl = nch;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int tot = __shfl_sync(0xffffffffu, incl, 31);
-        int base = 0;
-        if (lane == 31 && tot) base = atomicAdd(&st->nuitems, tot);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        const int first = base + incl - nch;
-        for (int c = 0; c < nch && first + c < a.uitems_cap; c++)
-            a.uitems[first + c] = make_int2(d, rb + 32 * c);
-    }
-    for (int o = 16; o > 0; o >>= 1) touched += __shfl_xor_sync(0xffffffffu, touched, o);
-    if (lane == 0 && touched) atomicAdd((unsigned long long *)&st->st_recomputed, touched);
-}
-
-// Support updates, one warp per item (a directed loss v loses w, and 32 of v's slots).
-// PASS 0 (stored balls still old) handles edges (v,z) with v < z and tests w in B_old(z);
-// PASS 1 (after the clears) handles v > z and tests w in B_new(z).  Distance is symmetric,
-// so w in B(z) is tested as z in B(w): all lanes read the same ball, at increasing z.
-template <int PASS>
+// Support updates, one warp per item (a directed loss v loses w, and <= 32 of v's slots),
+// both orientations in one pass against the stored balls of before this batch: an edge
+// (v,z) with v < z loses w from B(v) ∩ B(z) iff w in B_old(z); with v > z iff w in
+// B_new(z) = B_old(z) minus this batch's losses.  Distance is symmetric, so w in B(z) is
+// tested as z in B(w) (all lanes read one ball, at increasing z) and "w lost by z" as the
+// pair {w,z} in the lost-pair set.
 __device__ void ph_delta(const LossArgs &a) {
     __shared__ unsigned long long s_tests, s_bytes;
     DevStatus *st = a.st;
@@ -425,23 +480,20 @@ __device__ void ph_delta(const LossArgs &a) {
     __syncthreads();
     const int nitems = min(vload(st->nuitems), a.uitems_cap);
     const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
     unsigned long long tests = 0ull, bytes_total = 0ull;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nwarps) {
-        const int2 item = a.uitems[it];
-        const int4 L = a.lost[item.x >> 1];
-        const int v = (item.x & 1) ? L.y : L.x;
-        const int w = (item.x & 1) ? L.x : L.y;
+        const int4 item = a.uitems[it];  // (first slot, v, w, end of v's row)
+        const int v = item.y, w = item.z;
         const int2 wmeta = a.ball_meta[w];
-        const int re = a.row_ptr[v + 1];
-        const int sl = item.y + lane;
-        unsigned bytes = (lane == 0) ? 32u : 0u;  // item, loss record, row end, ball metadata
-        if (sl < re) {
+        const int sl = item.x + lane;
+        unsigned bytes = (lane == 0) ? 24u : 0u;  // item and w's ball metadata
+        if (sl < item.w) {
             const int z = a.col_live[sl];
             bytes += 4;
-            if (z >= 0 && (PASS == 0 ? (v < z) : (v > z))) {
+            if (z >= 0) {
                 tests++;
-                if (ball_contains_meta(a, wmeta, z, bytes)) {
+                if (ball_contains_meta(a, wmeta, z, bytes) && (v < z || !lost_now(a, w, z, bytes))) {
                     atomicSub(a.sup + a.slot_eid[sl], 1);
                     bytes += 12;
                 }
@@ -509,44 +561,105 @@ __device__ void ph_apply(const LossArgs &a) {
     if ((threadIdx.x & 31) == 0 && real) atomicAdd((unsigned long long *)&st->st_lost, real);
 }
 
-// Frontier selection and removal in one pass (incremental rounds): every alive edge with
-// h-support <= k-2 joins F and is removed at once (Algorithm 1, lines 7-10).
-__device__ void ph_select_remove(const LossArgs &a) {
+// Phase 1 of an incremental round: every alive edge with h-support <= k-2 joins F and is
+// removed at once (Algorithm 1, lines 7-10), and the loss detection items of its two edge
+// sides are written.  A continued round only writes the items of its remaining sides.
+__device__ void ph_select_items(const LossArgs &a) {
     DevStatus *st = a.st;
-    if (vload(st->cont)) return;  // a continued round keeps its (already removed) frontier
+    if (vload(st->cont)) {
+        ph_pair_items(a);
+        return;
+    }
     const int k = vload(st->k), round = vload(st->round), thr = k - 2;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); e0 < a.m; e0 += stride) {
-        const int64_t e = e0 + (threadIdx.x & 31);
-        const bool p = e < a.m && a.sup[e] <= thr;
-        warp_append(p, (int32_t)e, &st->nF, a.frontier_w);
-        if (p)
-            remove_edge((int)e, k, round, a.eu, a.ev, a.slot_lo, a.slot_hi, a.sup, a.truss,
-                        a.stamp_w, a.col_live_w, a.deg_alive_w, a.hub_slot, a.hub_bits_w, a.Wpad);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = 4 * (int64_t)gridDim.x * blockDim.x;
+    // four coalesced loads per thread per step, issued before any of them is used
+    for (int64_t e0 = 4 * (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)); e0 < a.m;
+         e0 += stride) {
+        int sv[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int64_t e = e0 + 32 * j + lane;
+            sv[j] = (e < a.m) ? a.sup[e] : INT_MAX;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int e = (int)(e0 + 32 * j + lane);
+            const bool p = sv[j] <= thr;
+            const unsigned bal = __ballot_sync(0xffffffffu, p);
+            if (bal == 0u) continue;
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&st->nF, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const int pos = base + __popc(bal & lanemask_lt());
+            int u_eu = 0, u_ev = 0, rb_u = 0, re_u = 0, rb_v = 0, re_v = 0, n0 = 0, n1 = 0;
+            if (p) {
+                a.frontier_w[pos] = e;
+                remove_edge(e, k, round, a.eu, a.ev, a.slot_lo, a.slot_hi, a.sup, a.truss,
+                            a.stamp_w, a.col_live_w, a.deg_alive_w, a.hub_slot, a.hub_bits_w, a.Wpad);
+                u_eu = a.eu[e];
+                u_ev = a.ev[e];
+                rb_u = a.row_ptr[u_eu];
+                re_u = a.row_ptr[u_eu + 1];
+                rb_v = a.row_ptr[u_ev];
+                re_v = a.row_ptr[u_ev + 1];
+                // side 0: eu with {ev} and N_old(ev); side 1: ev with N_old(eu); h = 1: {eu,ev}
+                n0 = (a.h < 2) ? 1 : (re_v - rb_v + 1 + 31) >> 5;
+                n1 = (a.h < 2) ? 0 : (re_u - rb_u + 31) >> 5;
+            }
+            int incl = n0 + n1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            int ibase = 0;
+            if (lane == 31 && tot) ibase = atomicAdd(&st->npitems, tot);
+            ibase = __shfl_sync(0xffffffffu, ibase, 31);
+            const int first = ibase + incl - (n0 + n1);
+            if (p && first + n0 > a.pitems_cap) atomicMin(&st->overflow_unit, 2 * pos);
+            if (p && n1 && first + n0 + n1 > a.pitems_cap) atomicMin(&st->overflow_unit, 2 * pos + 1);
+            unsigned todo = __ballot_sync(0xffffffffu, p);
+            while (todo) {
+                const int l = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int f = __shfl_sync(0xffffffffu, first, l);
+                const int c0 = __shfl_sync(0xffffffffu, n0, l), c1 = __shfl_sync(0xffffffffu, n1, l);
+                const int pl = __shfl_sync(0xffffffffu, pos, l);
+                const int xu = __shfl_sync(0xffffffffu, u_eu, l), xv = __shfl_sync(0xffffffffu, u_ev, l);
+                const int su = __shfl_sync(0xffffffffu, rb_u, l), sv0 = __shfl_sync(0xffffffffu, rb_v, l);
+                const bool fits0 = f + c0 <= a.pitems_cap, fits1 = f + c0 + c1 <= a.pitems_cap;
+                for (int c = lane; c < c0 + c1 && f + c < a.pitems_cap; c += 32) {
+                    if (c < c0)
+                        a.pitems[f + c] = fits0 ? make_int4(2 * pl, sv0 - 1 + 32 * c, xu, xv)
+                                                : make_int4(-1, 0, 0, 0);
+                    else
+                        a.pitems[f + c] = fits1 ? make_int4(2 * pl + 1, su + 32 * (c - c0), xv, xu)
+                                                : make_int4(-1, 0, 0, 0);
+                }
+            }
+        }
     }
 }
 
 // One launch per phase (the rounds of a CUDA graph).
-__global__ void __launch_bounds__(kBlock) k_pair_items(LossArgs a) {
+__global__ void __launch_bounds__(kBlock) k_inc_select(LossArgs a) {
     if (vload(a.st->alive) == 0) return;
-    ph_pair_items(a);
+    ph_select_items(a);
 }
 __global__ void __launch_bounds__(kBlock) k_loss_detect(LossArgs a) {
     if (vload(a.st->alive) == 0) return;
     ph_detect(a);
 }
-__global__ void __launch_bounds__(kBlock) k_loss_items(LossArgs a) {
-    if (vload(a.st->alive) == 0) return;
-    ph_loss_items(a);
-}
-template <int PASS>
 __global__ void __launch_bounds__(kBlock) k_loss_delta(LossArgs a) {
     if (vload(a.st->alive) == 0) return;
-    ph_delta<PASS>(a);
+    ph_delta(a);
 }
-__global__ void __launch_bounds__(kBlock) k_loss_apply(LossArgs a) {
+__global__ void __launch_bounds__(kBlock) k_loss_apply_reduce(LossArgs a) {
     if (vload(a.st->alive) == 0) return;
     ph_apply(a);
+    minreduce_body<kBlock / 32>(a.sup, a.m, a.st, 0);
 }
 
 constexpr int kPBlock = 512;  // threads per block of the persistent kernel
@@ -558,7 +671,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Persistent round kernel (cooperative launch, every block resident): runs up to
-// `max_slots` round slots, each the eight phases of an incremental round separated by grid
+// `max_slots` round slots, each the four phases of an incremental round separated by grid
 // barriers, and stops early once no edge is alive or an error is flagged.  Block 0 adds
 // the time of each phase to the status block.
 __global__ void __launch_bounds__(kPBlock, 3) k_rounds_persistent(LossArgs a, int max_slots) {
@@ -576,23 +689,17 @@ __global__ void __launch_bounds__(kPBlock, 3) k_rounds_persistent(LossArgs a, in
     };
     for (int slot = 0; slot < max_slots; slot++) {
         if (vload(st->alive) == 0 || vload(st->err) != 0) break;
-        ph_select_remove(a);
+        ph_select_items(a);
         if (!phase_done(0)) return;
-        ph_pair_items(a);
-        if (!phase_done(1)) return;
         ph_detect(a);
+        if (!phase_done(1)) return;
+        ph_delta(a);
         if (!phase_done(2)) return;
-        ph_loss_items(a);
-        if (!phase_done(3)) return;
-        ph_delta<0>(a);
-        if (!phase_done(4)) return;
+        // clearing the lost members touches balls and hash slots only; the reduction reads
+        // supports only, and its last block closes the round after every block did both
         ph_apply(a);
-        if (!phase_done(5)) return;
-        ph_delta<1>(a);
-        if (!phase_done(6)) return;
         minreduce_body<kPBlock / 32>(a.sup, a.m, st, 0);
-        if (!phase_done(7)) return;
-        if (timer) st->st_slots++;
+        if (!phase_done(3)) return;
     }
 }
 
@@ -644,8 +751,6 @@ LossArgs loss_args(Handle *H) {
 
 }  // namespace
 
-// Enqueues the loss detection and the support updates of one incremental round (after
-// k_remove, before the min reduction).  ev_mid (nullable) is recorded between the two.
 // Launches the persistent round kernel once (at most max_slots round slots).  The grid is
 // every block that can be resident at once, as a cooperative launch requires.
 htd_status launch_persistent_rounds(Handle *H, cudaStream_t s, int max_slots, int64_t *launches) {
@@ -659,7 +764,7 @@ htd_status launch_persistent_rounds(Handle *H, cudaStream_t s, int max_slots, in
             set_last_error("persistent round kernel: no resident block fits");
             return HTD_ECUDA;
         }
-        grid_cached = H->num_sms * occ;
+        grid_cached = std::min(H->num_sms * occ, 64 * 32);  // the grid barrier's limit
         dev_cached = H->g.device;
     }
     void *args[] = {&a, &max_slots};
@@ -673,21 +778,30 @@ htd_status launch_persistent_rounds(Handle *H, cudaStream_t s, int max_slots, in
     return HTD_OK;
 }
 
-htd_status enqueue_loss_kernels(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t ev_mid,
-                                unsigned record_flags) {
+// Enqueues one incremental round as four launches (the graph path).  evs (nullable):
+// kRoundEvents events; phases are marked as select | - | detect | update | - | reduce.
+htd_status enqueue_incremental_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t *evs,
+                                     unsigned record_flags) {
     LossArgs a = loss_args(H);
     const int grid = H->num_sms * 8;
-    k_pair_items<<<H->num_sms * 4, kBlock, 0, s>>>(a);
+    auto mark = [&](int i) {
+        if (evs) cudaEventRecordWithFlags(evs[i], s, record_flags);
+    };
+    mark(0);
+    k_inc_select<<<grid, kBlock, 0, s>>>(a);
+    mark(1);
+    mark(2);
     k_loss_detect<<<grid, kBlock, 0, s>>>(a);
-    if (ev_mid) cudaEventRecordWithFlags(ev_mid, s, record_flags);
-    k_loss_items<<<H->num_sms * 4, kBlock, 0, s>>>(a);
-    k_loss_delta<0><<<grid, kBlock, 0, s>>>(a);
-    k_loss_apply<<<grid, kBlock, 0, s>>>(a);
-    k_loss_delta<1><<<grid, kBlock, 0, s>>>(a);
-    *launches += 6;
+    mark(3);
+    k_loss_delta<<<grid, kBlock, 0, s>>>(a);
+    mark(4);
+    mark(5);
+    k_loss_apply_reduce<<<grid, kBlock, 0, s>>>(a);
+    mark(6);
+    *launches += 4;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
-        set_last_error(std::string("enqueue_loss_kernels: ") + cudaGetErrorString(e));
+        set_last_error(std::string("enqueue_incremental_round: ") + cudaGetErrorString(e));
         return HTD_ECUDA;
     }
     return HTD_OK;

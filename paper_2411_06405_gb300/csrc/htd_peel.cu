@@ -684,8 +684,9 @@ htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) 
     }
     if (incremental) {
         // a round's lost pairs: half of a power-of-two table of 8 x (2m) slots (>= 2^12)
+        // sized to stay L2-resident (at most 2^22 slots, 32 MiB); larger rounds run in batches
         int64_t cap = 4096;
-        while (cap < 16 * m && cap < ((int64_t)1 << 28)) cap <<= 1;
+        while (cap < 4 * m && cap < ((int64_t)1 << 22)) cap <<= 1;
         if (tiny_table) cap = 128;  // forces rounds to run in many batches
         w.lost_tiny = tiny_table;
         w.lost_cap = cap;
@@ -802,6 +803,10 @@ htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
                 cudaGraphExecDestroy(H->graph_exec);
                 H->graph_exec = nullptr;
             }
+            if (H->graph_exec_timed) {
+                cudaGraphExecDestroy(H->graph_exec_timed);
+                H->graph_exec_timed = nullptr;
+            }
         }
         ba.pool = w.pool;
         if (timing) HTD_CHECK(cudaEventRecord(e0, s));
@@ -855,25 +860,10 @@ htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent
     auto mark = [&](int i) {
         if (evs) cudaEventRecordWithFlags(evs[i], s, rec_flags);
     };
+    if (w.incremental) return enqueue_incremental_round(H, s, launches, evs, rec_flags);
     mark(0);
     k_select<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, w.frontier);
     mark(1);
-    if (w.incremental) {
-        k_remove<<<gsmall, kBlock, 0, s>>>(w.frontier, w.status, g.eu, g.ev, g.slot_lo, g.slot_hi,
-                                           w.sup, w.truss, w.stamp, w.col_live, w.deg_alive,
-                                           w.hub_slot, w.hub_bits, w.Wpad);
-        mark(2);
-        *launches += 2;
-        htd_status ls = enqueue_loss_kernels(H, s, launches, evs ? evs[3] : nullptr, rec_flags);
-        if (ls != HTD_OK) return ls;
-        mark(4);
-        mark(5);
-        k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 0);
-        mark(6);
-        (*launches)++;
-        HTD_CHECK(cudaGetLastError());
-        return HTD_OK;
-    }
     k_cand_init<<<gsmall, kBlock, 0, s>>>(w.frontier, g.eu, g.ev, w.status, w.cand_stamp, w.cand_list);
     *launches += 2;
     for (int d = 1; d < w.h; d++) {

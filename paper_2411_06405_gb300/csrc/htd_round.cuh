@@ -7,8 +7,9 @@
 
 namespace htd {
 
-// Spins of a grid barrier before it gives up (each spin sleeps about 0.1 us): about 2 s,
-// far longer than any phase; on expiry the barrier sets an error and the kernel returns.
+// Spins of a grid barrier before it gives up (after the first few thousand, each spin sleeps
+// about 0.1 us): about 2 s, far longer than any phase; on expiry the barrier sets an error
+// and the kernel returns.
 constexpr unsigned kBarrierSpinLimit = 1u << 24;
 
 // Removes edge e at level k in round `round` (Algorithm 1, lines 8-10): t(e) = k, its
@@ -60,6 +61,7 @@ __device__ __forceinline__ void round_finalize(DevStatus *st, int initial) {
         st->st_candidates += cands;
         st->st_changed += st->nchanged;
     }
+    if (!initial) st->st_slots++;
     st->alive = al;
     if (al > 0 && !unfinished) st->k = max(st->k, mn + 2);
     st->min_acc = INT_MAX;
@@ -88,12 +90,21 @@ __device__ __forceinline__ void minreduce_body(const int32_t *__restrict__ sup, 
     __shared__ bool s_last;
     int lmin = INT_MAX;
     long long lc = 0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int s = sup[e];
-        if (s != INT_MAX) {
-            lmin = min(lmin, s);
-            lc++;
+    // four coalesced loads per thread per step, issued before any of them is used
+    const int64_t stride = 4 * (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = 4 * (blockIdx.x * (int64_t)blockDim.x) + threadIdx.x; e0 < m; e0 += stride) {
+        int sv[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int64_t e = e0 + (int64_t)j * blockDim.x;
+            sv[j] = (e < m) ? sup[e] : INT_MAX;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (sv[j] != INT_MAX) {
+                lmin = min(lmin, sv[j]);
+                lc++;
+            }
         }
     }
     lmin = warp_min(lmin);
@@ -122,13 +133,15 @@ __device__ __forceinline__ void minreduce_body(const int32_t *__restrict__ sup, 
     __syncthreads();
 }
 
-// Barrier across all blocks of a cooperative launch (all co-resident).  The last block to
-// arrive resets the count and advances the generation; the others wait for the generation
-// to move, at most kBarrierSpinLimit spins.  Returns false (and sets an error) if the wait
-// gave up.  Memory written by any block before the barrier is visible to every thread after
-// it: each block fences before it arrives (release), its first thread fences again once
-// the generation has moved (acquire, which also drops stale lines from the SM's L1), and
-// the block-wide barrier then orders the block's other threads after that fence.
+// Barrier across all blocks of a cooperative launch (all co-resident, at most 64 x 32
+// blocks).  Arrivals are counted in two levels so that no counter takes more than 32
+// atomics per barrier: blocks count in their group of 32, the last block of a group counts
+// the group, and the last group advances the generation.  The others wait for the
+// generation to move, at most kBarrierSpinLimit spins; a wait that gives up sets an error
+// and returns false.  Memory written by any block before the barrier is visible to every
+// thread after it: each block fences before it arrives (release), its first thread fences
+// again once the generation has moved (acquire, which also drops stale lines from the SM's
+// L1), and the block-wide barrier then orders the block's other threads after that fence.
 __device__ __forceinline__ bool grid_barrier(DevStatus *st) {
     __shared__ int s_ok;
     __syncthreads();
@@ -136,10 +149,18 @@ __device__ __forceinline__ bool grid_barrier(DevStatus *st) {
         volatile unsigned *gen_p = &st->bar_gen;
         const unsigned gen = *gen_p;
         __threadfence();
-        const unsigned arrived = atomicAdd(&st->bar_count, 1u);
+        const unsigned g = blockIdx.x >> 5, ngroups = (gridDim.x + 31) >> 5;
+        const unsigned gsize = min(32u, gridDim.x - (g << 5));
+        bool release = false;
+        if (atomicAdd(&st->bar_group[g], 1u) == gsize - 1) {
+            atomicExch(&st->bar_group[g], 0u);  // every block of the group is waiting now
+            if (atomicAdd(&st->bar_count, 1u) == ngroups - 1) {
+                atomicExch(&st->bar_count, 0u);
+                release = true;
+            }
+        }
         int ok = 1;
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&st->bar_count, 0u);
+        if (release) {
             __threadfence();
             atomicAdd(&st->bar_gen, 1u);
         } else {
@@ -149,7 +170,7 @@ __device__ __forceinline__ bool grid_barrier(DevStatus *st) {
                     ok = 1;
                     break;
                 }
-                __nanosleep(100);
+                if (it >= 4096) __nanosleep(100);  // a long wait stops hammering the line
             }
             if (!ok) atomicOr(&st->err, kErrBarrierTimeout);
         }

@@ -135,7 +135,7 @@ def test_h_support_against_floyd_warshall(htd):
 
 # ---- a4-a7: peeling -----------------------------------------------------------------------------
 
-MODES = {"incremental": 0, "graph": 16, "rebuild": 4}
+MODES = {"incremental": 0, "persistent": 16, "rebuild": 4}
 
 
 @pytest.mark.parametrize("mode", sorted(MODES))
@@ -238,8 +238,8 @@ def test_graph_and_direct_launch_agree_and_repeat(htd, oracle_mod):
     assert torch.equal(t1, t2) and torch.equal(t1, t3) and torch.equal(t1, t5)
     assert torch.equal(st1, st5)  # same level-synchronous schedule
     assert s1["rounds"] == s2["rounds"] == s3["rounds"] == s5["rounds"]
-    assert s3["timed_slots"] >= s3["rounds"] and s3["ms_find"] > 0
-    assert s5["timed_slots"] >= s5["rounds"] and s5["ms_ball"] > 0
+    assert 0 < s3["timed_slots"] <= s3["slots"] and s3["ms_find"] > 0 and s3["slots"] >= s3["rounds"]
+    assert 0 < s5["timed_slots"] <= s5["slots"] and s5["ms_ball"] > 0
     assert s1["incremental"] == 1 and s5["incremental"] == 0
     # changing h on the same handle and coming back
     t_h3, _, _ = htd.htd_truss_decompose(g, 3)
@@ -279,9 +279,10 @@ def test_incremental_matches_rebuild_on_hubby_graph(htd):
     for h in (1, 2):
         a, sa, st_a = htd.htd_truss_decompose(g, h, stamps=True)
         b, sb, st_b = htd.htd_truss_decompose(g, h, stamps=True, flags=htd.HTD_OPT_REBUILD)
-        c, sc, st_c = htd.htd_truss_decompose(g, h, stamps=True, flags=htd.HTD_OPT_GRAPH_ROUNDS)
+        c, sc, st_c = htd.htd_truss_decompose(g, h, stamps=True,
+                                              flags=htd.HTD_OPT_PERSISTENT_ROUNDS)
         assert st_a["incremental"] == 1 and st_b["incremental"] == 0 and st_c["incremental"] == 1
-        assert st_a["round_kernel_launches"] >= 1 and st_c["round_kernel_launches"] == 0
+        assert st_a["round_kernel_launches"] == 0 and st_c["round_kernel_launches"] >= 1
         assert torch.equal(a, b) and torch.equal(sa, sb)
         assert torch.equal(a, c) and torch.equal(sa, sc)
 
@@ -296,7 +297,7 @@ def test_batched_rounds_match_oracle(htd, oracle_mod, h):
         t, stamp, st = htd.htd_truss_decompose(g, h, stamps=True,
                                                flags=htd.HTD_OPT_TINY_LOSS_TABLE)
         t2, stamp2, _ = htd.htd_truss_decompose(
-            g, h, stamps=True, flags=htd.HTD_OPT_TINY_LOSS_TABLE | htd.HTD_OPT_GRAPH_ROUNDS)
+            g, h, stamps=True, flags=htd.HTD_OPT_TINY_LOSS_TABLE | htd.HTD_OPT_PERSISTENT_ROUNDS)
         assert torch.equal(t, t2) and torch.equal(stamp, stamp2)
         t_ref, stamp_ref, rounds = og.truss_decompose(h)
         np.testing.assert_array_equal(host(t), t_ref)
