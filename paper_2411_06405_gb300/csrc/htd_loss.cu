@@ -233,35 +233,6 @@ __device__ __forceinline__ bool ball_contains(const LossArgs &a, int z, int w, u
 // record and the pair's update work (both rows are visited by the support updates) are
 // reserved against the batch limits; a pair that does not fit marks its edge side u as
 // the point where the next slot of this round resumes.
-__device__ __forceinline__ int record_lost(const LossArgs &a, DevStatus *st, int x, int z, int u,
-                                           unsigned &reads) {
-    if (!ball_contains(a, x, z, reads)) return -1;  // stored bit already clear
-    const long long work = (long long)(a.row_ptr[x + 1] - a.row_ptr[x]) +
-                           (a.row_ptr[z + 1] - a.row_ptr[z]);
-    const long long before =
-        (long long)atomicAdd((unsigned long long *)&st->upd_work, (unsigned long long)work);
-    const int idx = atomicAdd(&st->nlost, 1);
-    if (idx >= a.lost_max || before + work > a.upd_budget) {
-        atomicMin(&st->overflow_unit, u);
-        if (idx < a.lost_max) a.lost[idx] = make_int4(-1, -1, -1, 0);
-        return -1;
-    }
-    const unsigned long long key = pair_key(x, z);
-    unsigned long long slot = mix64(key) & a.cap_mask;
-    int4 rec = make_int4(-1, -1, -1, 0);  // null record: the pair is already held
-    for (unsigned long long probe = 0; probe <= a.cap_mask; probe++) {
-        const unsigned long long prev = atomicCAS(a.keys + slot, kEmpty, key);
-        if (prev == kEmpty) {
-            rec = make_int4(min(x, z), max(x, z), (int)slot, 0);
-            break;
-        }
-        if (prev == key) break;
-        slot = (slot + 1) & a.cap_mask;
-    }
-    a.lost[idx] = rec;
-    return rec.x >= 0 ? idx : -1;
-}
-
 // Is the pair {p,q} among this batch's lost pairs?
 __device__ __forceinline__ bool lost_now(const LossArgs &a, int p, int q, unsigned &bytes) {
     const unsigned long long key = pair_key(p, q);
@@ -276,35 +247,104 @@ __device__ __forceinline__ bool lost_now(const LossArgs &a, int p, int q, unsign
     return false;
 }
 
-// Update items of the new lost pairs of a warp, one pair per lane (rec >= 0): direction 0
-// = v0 = min loses v1, in runs of 32 of v0's slots; direction 1 = v1 loses v0.  Each lane
-// reserves and writes its own items when they are few; long rows are written by the whole
-// warp, one pair after the other.  Also counts, once per round and vertex, the alive edges
-// whose support the updates bring up to date.
-__device__ __forceinline__ void emit_update_items(const LossArgs &a, DevStatus *st, int rec, int x,
-                                                  int z, int round, unsigned long long &touched) {
+// Inclusive prefix sum over the warp.
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Records the lost pairs {x, z} of a warp (lanes with lost == true; all lanes call it).
+// A pair whose stored bit is already clear was handled by an earlier batch of this round
+// and is skipped.  Each record and its update work (both rows are visited by the support
+// updates) are reserved against the batch limits with one atomic per warp and counter; a
+// pair that does not fit marks its edge side u as the point where the next slot of this
+// round resumes.  New pairs go into the lost-pair set, and their update items (runs of 32
+// slots of each endpoint's row) are written: by their own lane when few, else by the warp.
+// Also counts, once per round and vertex, the alive edges whose support is brought up to
+// date.
+__device__ __forceinline__ void record_lost_warp(const LossArgs &a, DevStatus *st, bool lost, int x,
+                                                 int z, int u, int round, unsigned &reads,
+                                                 unsigned long long &touched) {
     constexpr int kOwnItems = 8;
     const int lane = threadIdx.x & 31;
-    int v0 = 0, v1 = 0, rb0 = 0, re0 = 0, rb1 = 0, re1 = 0, n0 = 0, n1 = 0, base = 0;
-    if (rec >= 0) {
-        v0 = min(x, z);
-        v1 = max(x, z);
-        rb0 = a.row_ptr[v0];
-        re0 = a.row_ptr[v0 + 1];
-        rb1 = a.row_ptr[v1];
-        re1 = a.row_ptr[v1 + 1];
-        n0 = (re0 - rb0 + 31) >> 5;
-        n1 = (re1 - rb1 + 31) >> 5;
-        base = atomicAdd(&st->nuitems, n0 + n1);
-        if (atomicExch(a.vtouch + v0, round) != round) touched += a.deg_alive[v0];
-        if (atomicExch(a.vtouch + v1, round) != round) touched += a.deg_alive[v1];
-        if (n0 + n1 <= kOwnItems) {
-            for (int c = 0; c < n0 + n1 && base + c < a.uitems_cap; c++)
-                a.uitems[base + c] = (c < n0) ? make_int4(rb0 + 32 * c, v0, v1, re0)
-                                              : make_int4(rb1 + 32 * (c - n0), v1, v0, re1);
+    const bool want = lost && ball_contains(a, x, z, reads);
+    int rbx = 0, rex = 0, rbz = 0, rez = 0;
+    long long work = 0;
+    if (want) {
+        rbx = a.row_ptr[x];
+        rex = a.row_ptr[x + 1];
+        rbz = a.row_ptr[z];
+        rez = a.row_ptr[z + 1];
+        work = (long long)(rex - rbx) + (rez - rbz);
+    }
+    const unsigned wantb = __ballot_sync(0xffffffffu, want);
+    if (wantb == 0u) return;
+    const long long wincl = warp_incl_scan(work);
+    const int rank = __popc(wantb & lanemask_lt());
+    const long long wtot = __shfl_sync(0xffffffffu, wincl, 31);
+    long long wbase = 0;
+    int ibase = 0;
+    if (lane == 0) {
+        wbase = (long long)atomicAdd((unsigned long long *)&st->upd_work, (unsigned long long)wtot);
+        ibase = atomicAdd(&st->nlost, __popc(wantb));
+    }
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    ibase = __shfl_sync(0xffffffffu, ibase, 0);
+    int rec_idx = -1;
+    if (want) {
+        const int idx = ibase + rank;
+        if (idx >= a.lost_max || wbase + wincl > a.upd_budget) {
+            atomicMin(&st->overflow_unit, u);
+            if (idx < a.lost_max) a.lost[idx] = make_int4(-1, -1, -1, 0);
+        } else {
+            const unsigned long long key = pair_key(x, z);
+            unsigned long long slot = mix64(key) & a.cap_mask;
+            int4 rec = make_int4(-1, -1, -1, 0);  // null record: the pair is already held
+            for (unsigned long long probe = 0; probe <= a.cap_mask; probe++) {
+                const unsigned long long prev = atomicCAS(a.keys + slot, kEmpty, key);
+                if (prev == kEmpty) {
+                    rec = make_int4(min(x, z), max(x, z), (int)slot, 0);
+                    break;
+                }
+                if (prev == key) break;
+                slot = (slot + 1) & a.cap_mask;
+            }
+            a.lost[idx] = rec;
+            if (rec.x >= 0) rec_idx = idx;
         }
     }
-    unsigned big = __ballot_sync(0xffffffffu, rec >= 0 && n0 + n1 > kOwnItems);
+    // update items: direction 0 = v0 = min loses v1, direction 1 = v1 loses v0
+    int v0 = 0, v1 = 0, rb0 = 0, re0 = 0, rb1 = 0, re1 = 0, n0 = 0, n1 = 0;
+    if (rec_idx >= 0) {
+        const bool xf = x < z;
+        v0 = xf ? x : z;
+        v1 = xf ? z : x;
+        rb0 = xf ? rbx : rbz;
+        re0 = xf ? rex : rez;
+        rb1 = xf ? rbz : rbx;
+        re1 = xf ? rez : rex;
+        n0 = (re0 - rb0 + 31) >> 5;
+        n1 = (re1 - rb1 + 31) >> 5;
+        if (atomicExch(a.vtouch + v0, round) != round) touched += a.deg_alive[v0];
+        if (atomicExch(a.vtouch + v1, round) != round) touched += a.deg_alive[v1];
+    }
+    const int nincl = warp_incl_scan(n0 + n1);
+    int nbase = 0;
+    if (lane == 31 && nincl) nbase = atomicAdd(&st->nuitems, nincl);
+    nbase = __shfl_sync(0xffffffffu, nbase, 31);
+    const int base = nbase + nincl - (n0 + n1);
+    if (rec_idx >= 0 && n0 + n1 <= kOwnItems) {
+        for (int c = 0; c < n0 + n1 && base + c < a.uitems_cap; c++)
+            a.uitems[base + c] = (c < n0) ? make_int4(rb0 + 32 * c, v0, v1, re0)
+                                          : make_int4(rb1 + 32 * (c - n0), v1, v0, re1);
+    }
+    unsigned big = __ballot_sync(0xffffffffu, rec_idx >= 0 && n0 + n1 > kOwnItems);
     while (big) {
         const int l = __ffs(big) - 1;
         big &= big - 1;
@@ -443,8 +483,7 @@ __device__ void ph_detect(const LossArgs &a) {
             const bool kept = warp_common_neighbour(a, hp, hq, reads);
             if (lane == leader) state = kept ? kKept : kLost;
         }
-        const int rec = (state == kLost) ? record_lost(a, st, r.x, z, u, reads) : -1;
-        emit_update_items(a, st, rec, r.x, z, round, touched);
+        record_lost_warp(a, st, state == kLost, r.x, z, u, round, reads, touched);
         reads_total += reads;
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -787,8 +826,11 @@ htd_status enqueue_incremental_round(Handle *H, cudaStream_t s, int64_t *launche
     auto mark = [&](int i) {
         if (evs) cudaEventRecordWithFlags(evs[i], s, record_flags);
     };
+    // the two scans over all edges use fewer blocks: the reduction's per-block atomics all
+    // hit the same few counters
+    const int grid_scan = H->num_sms * 2;
     mark(0);
-    k_inc_select<<<grid, kBlock, 0, s>>>(a);
+    k_inc_select<<<grid_scan, kBlock, 0, s>>>(a);
     mark(1);
     mark(2);
     k_loss_detect<<<grid, kBlock, 0, s>>>(a);
@@ -796,7 +838,7 @@ htd_status enqueue_incremental_round(Handle *H, cudaStream_t s, int64_t *launche
     k_loss_delta<<<grid, kBlock, 0, s>>>(a);
     mark(4);
     mark(5);
-    k_loss_apply_reduce<<<grid, kBlock, 0, s>>>(a);
+    k_loss_apply_reduce<<<grid_scan, kBlock, 0, s>>>(a);
     mark(6);
     *launches += 4;
     cudaError_t e = cudaGetLastError();
