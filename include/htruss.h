@@ -72,7 +72,7 @@ typedef struct htd_stats {
     int64_t pairs_lost;      /* incremental rounds: pairs that left each other's balls */
     int64_t member_tests;    /* incremental rounds: ball-membership tests of support updates */
     int64_t kernel_launches; /* kernels this library launched for the call */
-    int64_t ball_pool_bytes; /* device bytes held by the h-hop balls */
+    int64_t ball_pool_bytes; /* device bytes the stored h-hop balls take */
     int64_t timed_slots;     /* round slots whose phases were timed (with HTD_OPT_TIMING the
                                 graph path times every 8th batch of 16 slots) */
     double alg_bytes_ball;   /* algorithmic bytes: ball builds (initial and rebuilds) */
@@ -106,6 +106,12 @@ typedef struct htd_stats {
                                           a CUDA graph of 16 rounds (same results) */
 #define HTD_OPT_TINY_LOSS_TABLE 8u  /* h <= 2: 128-slot lost-pair table, so that rounds run in
                                        many batches (a test of that path; slow) */
+#define HTD_OPT_COMPACT_BALLS 32u   /* h <= 2: store each ball in its smaller form (sorted
+                                       non-zero words when at most half the words are
+                                       non-zero) even when every ball fits dense; by default
+                                       the incremental peel keeps all balls dense (one load
+                                       per membership test) when the n x n bits fit in a
+                                       quarter of the free device memory (same results) */
 
 /* Normalise an undirected edge list and build the graph (Sec. 2 graph model).
  *   n            vertex count, ids in [0, n); 0 <= n <= HTD_MAX_N.

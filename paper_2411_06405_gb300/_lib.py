@@ -24,6 +24,7 @@ HTD_OPT_NO_GRAPH = 2
 HTD_OPT_REBUILD = 4
 HTD_OPT_TINY_LOSS_TABLE = 8
 HTD_OPT_PERSISTENT_ROUNDS = 16
+HTD_OPT_COMPACT_BALLS = 32
 
 # every symbol include/htruss.h declares
 EXPORTED = (

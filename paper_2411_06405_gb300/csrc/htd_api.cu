@@ -247,6 +247,7 @@ htd_status htd_h_support(htd_graph *g, int32_t h, int32_t *sup_dev, void *stream
     cudaStream_t user = static_cast<cudaStream_t>(stream);
     API_TRY(begin_call(H, user));
     API_TRY(prepare_work(H, h, true));
+    H->w.dense_balls = false;  // h-support alone streams the smaller form of each ball
     int64_t launches = 0;
     htd_status ip = htd::initial_pass(H, h, H->pstream, &launches, nullptr);
     htd::g_launches += launches;
@@ -286,6 +287,15 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
     bool incremental = (flags & HTD_OPT_REBUILD) == 0;
     API_TRY(prepare_work(H, h, incremental, (flags & HTD_OPT_TINY_LOSS_TABLE) != 0));
     incremental = w.incremental;
+    // the incremental peel's membership tests take one load on a dense ball, a binary search
+    // on a compact one: keep every ball dense when the n x n bits fit comfortably
+    w.dense_balls = false;
+    if (incremental && (flags & HTD_OPT_COMPACT_BALLS) == 0) {
+        size_t free_b = 0, total_b = 0;
+        API_CHECK(cudaMemGetInfo(&free_b, &total_b));
+        const double dense_bytes = 4.0 * (double)H->g.n * (double)w.Wpad;
+        w.dense_balls = dense_bytes <= (double)free_b / 4 && dense_bytes < 4.0 * (double)((int64_t)1 << 33);
+    }
     {
         htd_status ip = htd::initial_pass(H, h, H->pstream, &launches, timing ? &local : nullptr);
         htd::g_launches += launches;
@@ -487,7 +497,7 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
         local.alg_bytes_detect = (double)s->st_bytes_detect;
         local.alg_bytes_update = (double)s->st_bytes_update;
         local.kernel_launches = launches;
-        local.ball_pool_bytes = w.pool_words * 4;
+        local.ball_pool_bytes = w.pool_used * 4;
         *stats = local;
     }
     return HTD_OK;

@@ -32,6 +32,7 @@ struct PeelWork {
     int32_t W = 0;                 // 32-bit words of an n-bit set
     int32_t Wpad = 0;              // W rounded up to a multiple of 4
     int64_t pool_words = 0;        // ball storage size (uint32 words)
+    int64_t pool_used = 0;         // words the balls of the last initial pass took
     uint32_t *pool = nullptr;      // ball storage
     int64_t *ball_off = nullptr;   // n+1 offsets into pool (multiples of 4 words)
     int32_t *ball_need = nullptr;  // n storage words of the initial balls
@@ -51,6 +52,7 @@ struct PeelWork {
     int2 *items = nullptr;         // (vertex, first slot) h-support work items
     int64_t items_cap = 0;
     bool incremental = false;      // h <= 2: lost-pair support updates instead of rebuilds
+    bool dense_balls = false;      // every ball stored dense (set per call before the initial pass)
     unsigned long long *lost_keys = nullptr;  // hash set of the round's lost pairs
     int64_t lost_cap = 0;          // hash slots (power of two)
     int64_t lost_max = 0;          // lost-pair records one batch may hold (half the slots)

@@ -41,6 +41,7 @@ enum BallMode { kModeCount = 0, kModeStore = 1, kModeRebuild = 2 };
 struct BallArgs {
     int32_t n, W, Wpad, h;
     int32_t count_bytes;
+    int32_t force_dense;  // store every ball dense whatever its size
     const int32_t *row_ptr;
     const int32_t *col_live;
     const int32_t *deg_alive;
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kBlock) k_ball(BallArgs a) {
             nzw += s_wnz[j];
             if (j < wid) wbase += s_wnz[j];
         }
-        const bool dense = 2 * nzw > W;
+        const bool dense = a.force_dense || 2 * nzw > W;
         const int stor = dense ? a.Wpad : ((2 * nzw + 3) & ~3);
         bool store = true;
         if (MODE == kModeCount) {
@@ -545,6 +546,7 @@ BallArgs ball_args(Handle *H) {
     a.Wpad = w.Wpad;
     a.h = w.h;
     a.count_bytes = 1;
+    a.force_dense = w.dense_balls ? 1 : 0;
     a.row_ptr = g.row_ptr;
     a.col_live = w.col_live;
     a.deg_alive = w.deg_alive;
@@ -809,6 +811,7 @@ htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
             }
         }
         ba.pool = w.pool;
+        w.pool_used = total;
         if (timing) HTD_CHECK(cudaEventRecord(e0, s));
         k_ball<kModeStore><<<w.grid_ball, kBlock, w.smem_ball, s>>>(ba);
         if (timing) HTD_CHECK(cudaEventRecord(e1, s));

@@ -135,7 +135,8 @@ def test_h_support_against_floyd_warshall(htd):
 
 # ---- a4-a7: peeling -----------------------------------------------------------------------------
 
-MODES = {"incremental": 0, "persistent": 16, "rebuild": 4}
+# incremental peels keep all balls dense when they fit; "compact" stores the smaller form
+MODES = {"incremental": 0, "persistent": 16, "rebuild": 4, "compact": 32}
 
 
 @pytest.mark.parametrize("mode", sorted(MODES))
@@ -281,10 +282,14 @@ def test_incremental_matches_rebuild_on_hubby_graph(htd):
         b, sb, st_b = htd.htd_truss_decompose(g, h, stamps=True, flags=htd.HTD_OPT_REBUILD)
         c, sc, st_c = htd.htd_truss_decompose(g, h, stamps=True,
                                               flags=htd.HTD_OPT_PERSISTENT_ROUNDS)
+        d, sd, st_d = htd.htd_truss_decompose(g, h, stamps=True, flags=htd.HTD_OPT_COMPACT_BALLS)
         assert st_a["incremental"] == 1 and st_b["incremental"] == 0 and st_c["incremental"] == 1
         assert st_a["round_kernel_launches"] == 0 and st_c["round_kernel_launches"] >= 1
+        # all-dense storage takes n x W words; the compact form is smaller on this graph
+        assert st_d["ball_pool_bytes"] < st_a["ball_pool_bytes"]
         assert torch.equal(a, b) and torch.equal(sa, sb)
         assert torch.equal(a, c) and torch.equal(sa, sc)
+        assert torch.equal(a, d) and torch.equal(sa, sd)
 
 
 @pytest.mark.parametrize("h", [1, 2])
@@ -298,7 +303,10 @@ def test_batched_rounds_match_oracle(htd, oracle_mod, h):
                                                flags=htd.HTD_OPT_TINY_LOSS_TABLE)
         t2, stamp2, _ = htd.htd_truss_decompose(
             g, h, stamps=True, flags=htd.HTD_OPT_TINY_LOSS_TABLE | htd.HTD_OPT_PERSISTENT_ROUNDS)
+        t3, stamp3, _ = htd.htd_truss_decompose(
+            g, h, stamps=True, flags=htd.HTD_OPT_TINY_LOSS_TABLE | htd.HTD_OPT_COMPACT_BALLS)
         assert torch.equal(t, t2) and torch.equal(stamp, stamp2)
+        assert torch.equal(t, t3) and torch.equal(stamp, stamp3)
         t_ref, stamp_ref, rounds = og.truss_decompose(h)
         np.testing.assert_array_equal(host(t), t_ref)
         np.testing.assert_array_equal(host(stamp), stamp_ref)  # same rounds as the oracle
