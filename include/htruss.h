@@ -74,7 +74,7 @@ typedef struct htd_stats {
     int64_t kernel_launches; /* kernels this library launched for the call */
     int64_t ball_pool_bytes; /* device bytes the stored h-hop balls take */
     int64_t timed_slots;     /* round slots whose phases were timed (with HTD_OPT_TIMING the
-                                graph path times every 8th batch of 16 slots) */
+                                graph path times every 16th batch of 16 slots) */
     double alg_bytes_ball;   /* algorithmic bytes: ball builds (initial and rebuilds) */
     double alg_bytes_hsup;   /* algorithmic bytes: full h-support intersections */
     double alg_bytes_detect; /* algorithmic bytes: loss detection (incremental rounds) */

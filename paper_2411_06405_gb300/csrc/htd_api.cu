@@ -364,7 +364,7 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
         // Graph path: R rounds per graph launch.  With HTD_OPT_TIMING a second graph with an
         // external event record at every phase boundary runs every kTimedEvery-th batch (the
         // events would otherwise slow every round); per-launch averages come from those.
-        constexpr int kTimedEvery = 8;
+        constexpr int kTimedEvery = 16;
         if (timing && H->round_events.empty()) {
             H->round_events.resize(htd::kRoundEvents * R, nullptr);
             for (auto &e : H->round_events) API_CHECK(cudaEventCreate(&e));
@@ -394,12 +394,15 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
             }
             return HTD_OK;
         };
-        if (use_graph && (!H->graph_exec || H->graph_h != h || H->graph_incremental != incremental)) {
+        // the captured kernel arguments fix h, the round variant and the ball layout
+        if (use_graph && (!H->graph_exec || H->graph_h != h || H->graph_incremental != incremental ||
+                          H->graph_dense != w.dense_balls)) {
             destroy_graph(H);
             API_TRY(capture(&H->graph_exec, nullptr));
             H->graph_h = h;
             H->graph_rounds = R;
             H->graph_incremental = incremental;
+            H->graph_dense = w.dense_balls;
         }
         if (use_graph && timing && !H->graph_exec_timed)
             API_TRY(capture(&H->graph_exec_timed, H->round_events.data()));

@@ -39,7 +39,7 @@ struct PeelWork {
     int32_t *ball_size = nullptr;  // n members of each ball (the vertex itself included)
     int32_t *ball_nw = nullptr;    // n: -1 = dense (W words), else (index,bits) pair count
     int2 *ball_meta = nullptr;     // n: (offset / 4, ball_nw) packed for one-load lookups
-    int32_t *col_live = nullptr;   // 2m neighbour ids, ~id once the edge is removed
+    int32_t *col_live = nullptr;   // 2m neighbour ids; -(round + 1) once removed in that round
     int32_t *deg_alive = nullptr;  // n alive degrees
     int32_t *sup = nullptr;        // m h-support (INT_MAX once removed)
     int32_t *truss = nullptr;      // m (points at the caller's output during a peel)
@@ -92,6 +92,7 @@ struct Handle {
     int graph_h = 0;
     int graph_rounds = 0;
     bool graph_incremental = false;
+    bool graph_dense = false;      // ball layout the captured rounds address directly
     int num_sms = 0;
 };
 

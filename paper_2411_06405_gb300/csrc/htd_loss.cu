@@ -68,6 +68,8 @@ struct LossArgs {
     const int32_t *hub_slot;
     const uint32_t *hub_bits;
     int32_t Wpad;
+    int32_t dense_all;  // every ball dense at pool + x * Wpad (no metadata lookup)
+    int32_t hub_all;    // every vertex has its alive-adjacency set, at row x
     int32_t pitems_cap;
     int4 *pitems;
     int32_t uitems_cap;
@@ -100,6 +102,7 @@ __device__ __forceinline__ T vload(const T &x) {
 
 // Alive-adjacency set of p if p has one (high degree), else null.
 __device__ __forceinline__ const uint32_t *hub_set(const LossArgs &a, int p, unsigned &reads) {
+    if (a.hub_all) return a.hub_bits + (int64_t)p * a.Wpad;
     reads++;
     const int hs = a.hub_slot[p];
     return hs >= 0 ? a.hub_bits + (int64_t)hs * a.Wpad : nullptr;
@@ -155,7 +158,7 @@ __device__ __forceinline__ int pair_quick(const LossArgs &a, int &p, int &q, uns
     if (alive_adjacent_set(a, qset, q, p, reads)) return kKept;
     if (a.h < 2) return kLost;
     // with q's set every scanned neighbour costs one read; without it, a binary search
-    if (min(dp, dq) > (qset ? 8 * kInlineScan : kInlineScan)) return kHard;
+    if (min(dp, dq) > kInlineScan) return kHard;
     const int rb = a.row_ptr[p], re = a.row_ptr[p + 1];
     // four slots at a time: their loads (and their set lookups) are independent
     for (int s0 = rb; s0 < re; s0 += 4) {
@@ -172,31 +175,73 @@ __device__ __forceinline__ int pair_quick(const LossArgs &a, int &p, int &q, uns
     return kLost;
 }
 
-// Common alive neighbour of p (shorter row) and q, searched by the whole warp: lanes take
-// p's slots 32 at a time and binary-search them in q's row; stops at the first hit.
-__device__ __forceinline__ bool warp_common_neighbour(const LossArgs &a, int p, int q,
-                                                      unsigned &reads) {
+// Inclusive prefix sum over the warp.
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
     const int lane = threadIdx.x & 31;
-    const int rb = a.row_ptr[p], re = a.row_ptr[p + 1];
-    const uint32_t *qset = hub_set(a, q, reads);
-    for (int s0 = rb; s0 < re; s0 += 128) {
-        int y[4];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Common alive neighbours for the warp's hard pairs (lanes with state == kHard; p the
+// shorter row), all at once: the pairs' rows of p are laid end to end and the warp walks
+// the concatenation 128 slots per step, each lane finding the pair its slot belongs to by a
+// binary search over the lanes' running row lengths.  A pair is kept at its first alive
+// neighbour that q also has; the walk skips kept pairs and stops once none is pending.
+// Called by whole warps.
+__device__ __forceinline__ void warp_hard_pairs(const LossArgs &a, int &state, int p, int q,
+                                                unsigned &reads) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool hard = state == kHard;
+    int rb = 0, len = 0;
+    const uint32_t *qset = nullptr;
+    if (hard) {
+        rb = a.row_ptr[p];
+        len = a.row_ptr[p + 1] - rb;
+        qset = hub_set(a, q, reads);
+        reads += 2;
+    }
+    const int incl = warp_incl_scan(len);
+    const int excl = incl - len;
+    const int total = __shfl_sync(full, incl, 31);
+    unsigned pending = __ballot_sync(full, hard);
+    unsigned kept = 0u;
+    for (int base = 0; base < total && pending; base += 128) {
+        int y[4], own[4];
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const int s = s0 + 32 * j + lane;
-            y[j] = (s < re) ? a.col_live[s] : -1;
+            const int idx = base + 32 * j + lane;
+            // owner lane: the number of lanes whose rows end at or before idx
+            int o = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(full, incl, o + step - 1) <= idx) o += step;
+            o = min(o, 31);
+            const int ex = __shfl_sync(full, excl, o), rbo = __shfl_sync(full, rb, o);
+            own[j] = o;
+            y[j] = (idx < total && ((pending >> o) & 1u)) ? a.col_live[rbo + idx - ex] : -1;
         }
-        bool hit = false;
+        unsigned hits = 0u;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
+            const int qo = __shfl_sync(full, q, own[j]);
+            const uint32_t *qs = reinterpret_cast<const uint32_t *>(
+                __shfl_sync(full, reinterpret_cast<unsigned long long>(qset), own[j]));
             if (y[j] >= 0) {
                 reads++;
-                hit |= alive_adjacent_set(a, qset, q, y[j], reads);
+                if (alive_adjacent_set(a, qs, qo, y[j], reads)) hits |= 1u << own[j];
             }
         }
-        if (__any_sync(0xffffffffu, hit)) return true;
+        hits = __reduce_or_sync(full, hits);
+        kept |= hits;
+        pending &= ~hits;
     }
-    return false;
+    if (hard) state = ((kept >> lane) & 1u) ? kKept : kLost;
 }
 
 // Is w in the stored ball of z (dense words, or sorted (word index, word) pairs)?
@@ -225,6 +270,10 @@ __device__ __forceinline__ bool ball_contains_meta(const LossArgs &a, int2 meta,
 }
 
 __device__ __forceinline__ bool ball_contains(const LossArgs &a, int z, int w, unsigned &bytes) {
+    if (a.dense_all) {
+        bytes += 4;
+        return (a.pool[(int64_t)z * a.Wpad + (w >> 5)] >> (w & 31)) & 1u;
+    }
     bytes += 8;
     return ball_contains_meta(a, a.ball_meta[z], w, bytes);
 }
@@ -247,18 +296,6 @@ __device__ __forceinline__ bool lost_now(const LossArgs &a, int p, int q, unsign
     return false;
 }
 
-// Inclusive prefix sum over the warp.
-template <typename T>
-__device__ __forceinline__ T warp_incl_scan(T v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const T t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-    }
-    return v;
-}
-
 // Records the lost pairs {x, z} of a warp (lanes with lost == true; all lanes call it).
 // A pair whose stored bit is already clear was handled by an earlier batch of this round
 // and is skipped.  Each record and its update work (both rows are visited by the support
@@ -266,11 +303,8 @@ __device__ __forceinline__ T warp_incl_scan(T v) {
 // pair that does not fit marks its edge side u as the point where the next slot of this
 // round resumes.  New pairs go into the lost-pair set, and their update items (runs of 32
 // slots of each endpoint's row) are written: by their own lane when few, else by the warp.
-// Also counts, once per round and vertex, the alive edges whose support is brought up to
-// date.
 __device__ __forceinline__ void record_lost_warp(const LossArgs &a, DevStatus *st, bool lost, int x,
-                                                 int z, int u, int round, unsigned &reads,
-                                                 unsigned long long &touched) {
+                                                 int z, int u, unsigned &reads) {
     constexpr int kOwnItems = 8;
     const int lane = threadIdx.x & 31;
     const bool want = lost && ball_contains(a, x, z, reads);
@@ -331,8 +365,6 @@ __device__ __forceinline__ void record_lost_warp(const LossArgs &a, DevStatus *s
         re1 = xf ? rez : rex;
         n0 = (re0 - rb0 + 31) >> 5;
         n1 = (re1 - rb1 + 31) >> 5;
-        if (atomicExch(a.vtouch + v0, round) != round) touched += a.deg_alive[v0];
-        if (atomicExch(a.vtouch + v1, round) != round) touched += a.deg_alive[v1];
     }
     const int nincl = warp_incl_scan(n0 + n1);
     int nbase = 0;
@@ -425,12 +457,11 @@ __device__ void ph_pair_items(const LossArgs &a) {
 }
 
 // Loss detection, one warp per item: lane i tests the pair of slot item.y + i.  A pair is
-// kept if its endpoints are adjacent or (h = 2) share an alive neighbour; lanes whose test
-// needs a long row scan hand it to the whole warp, one pair after the other.
+// kept if its endpoints are adjacent or (h = 2) share an alive neighbour; the pairs whose
+// test needs a longer row scan are walked by the whole warp together.
 __device__ void ph_detect(const LossArgs &a) {
     __shared__ unsigned long long s_pairs, s_reads;
     DevStatus *st = a.st;
-    unsigned long long touched = 0ull;
     if (threadIdx.x == 0) {
         s_pairs = 0ull;
         s_reads = 0ull;
@@ -457,16 +488,10 @@ __device__ void ph_detect(const LossArgs &a) {
             if (sl < r.rb) {
                 z = r.y;
             } else {
-                const int c = a.col[sl];
+                // an old neighbour: alive, or removed in this round
+                const int c = a.col[sl], cl = a.col_live[sl];
                 reads += 2;
-                if (c != r.x) {
-                    if (a.col_live[sl] >= 0) {
-                        z = c;
-                    } else {
-                        reads += 2;
-                        if (a.stamp[a.slot_eid[sl]] == round) z = c;
-                    }
-                }
+                if (c != r.x && (cl >= 0 || cl == -(round + 1))) z = c;
             }
         }
         int state = kKept, p = r.x, q = z;
@@ -474,24 +499,14 @@ __device__ void ph_detect(const LossArgs &a) {
             pairs++;
             state = pair_quick(a, p, q, reads);
         }
-        unsigned hard = __ballot_sync(0xffffffffu, state == kHard);
-        while (hard) {
-            const int leader = __ffs(hard) - 1;
-            hard &= hard - 1;
-            const int hp = __shfl_sync(0xffffffffu, p, leader);
-            const int hq = __shfl_sync(0xffffffffu, q, leader);
-            const bool kept = warp_common_neighbour(a, hp, hq, reads);
-            if (lane == leader) state = kept ? kKept : kLost;
-        }
-        record_lost_warp(a, st, state == kLost, r.x, z, u, round, reads, touched);
+        if (__any_sync(0xffffffffu, state == kHard)) warp_hard_pairs(a, state, p, q, reads);
+        record_lost_warp(a, st, state == kLost, r.x, z, u, reads);
         reads_total += reads;
     }
     for (int o = 16; o > 0; o >>= 1) {
         pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
         reads_total += __shfl_xor_sync(0xffffffffu, reads_total, o);
-        touched += __shfl_xor_sync(0xffffffffu, touched, o);
     }
-    if (lane == 0 && touched) atomicAdd((unsigned long long *)&st->st_recomputed, touched);
     if (lane == 0 && pairs) {
         atomicAdd(&s_pairs, pairs);
         atomicAdd(&s_reads, reads_total);
@@ -521,24 +536,49 @@ __device__ void ph_delta(const LossArgs &a) {
     const int lane = threadIdx.x & 31;
     unsigned long long tests = 0ull, bytes_total = 0ull;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nwarps) {
-        const int4 item = a.uitems[it];  // (first slot, v, w, end of v's row)
-        const int v = item.y, w = item.z;
-        const int2 wmeta = a.ball_meta[w];
-        const int sl = item.x + lane;
-        unsigned bytes = (lane == 0) ? 24u : 0u;  // item and w's ball metadata
-        if (sl < item.w) {
-            const int z = a.col_live[sl];
-            bytes += 4;
-            if (z >= 0) {
+    // two items per warp and step, their loads interleaved
+    constexpr int U = 2;
+    for (int it0 = U * ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); it0 < nitems;
+         it0 += U * nwarps) {
+        int4 item[U];  // (first slot, v, w, end of v's row)
+#pragma unroll
+        for (int j = 0; j < U; j++)
+            item[j] = (it0 + j < nitems) ? a.uitems[it0 + j] : make_int4(0, 0, 0, 0);
+        int z[U], eid[U];
+        bool in_w[U];
+#pragma unroll
+        for (int j = 0; j < U; j++) {
+            const int sl = item[j].x + lane;
+            const bool ok = sl < item[j].w;
+            z[j] = ok ? a.col_live[sl] : -1;
+            eid[j] = ok ? a.slot_eid[sl] : 0;
+            if (lane == 0 && it0 + j < nitems) bytes_total += a.dense_all ? 16u : 24u;
+            if (ok) bytes_total += 4;
+        }
+#pragma unroll
+        for (int j = 0; j < U; j++) {
+            in_w[j] = false;
+            if (z[j] >= 0) {
                 tests++;
-                if (ball_contains_meta(a, wmeta, z, bytes) && (v < z || !lost_now(a, w, z, bytes))) {
-                    atomicSub(a.sup + a.slot_eid[sl], 1);
-                    bytes += 12;
+                unsigned bytes = 0;
+                if (a.dense_all) {
+                    in_w[j] = (a.pool[(int64_t)item[j].z * a.Wpad + (z[j] >> 5)] >> (z[j] & 31)) & 1u;
+                    bytes += 4;
+                } else {
+                    in_w[j] = ball_contains(a, item[j].z, z[j], bytes);
                 }
+                bytes_total += bytes;
             }
         }
-        bytes_total += bytes;
+#pragma unroll
+        for (int j = 0; j < U; j++) {
+            unsigned bytes = 0;
+            if (in_w[j] && (item[j].y < z[j] || !lost_now(a, item[j].z, z[j], bytes))) {
+                atomicSub(a.sup + eid[j], 1);
+                bytes += 8;
+            }
+            bytes_total += bytes;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         tests += __shfl_xor_sync(0xffffffffu, tests, o);
@@ -555,35 +595,42 @@ __device__ void ph_delta(const LossArgs &a) {
     }
 }
 
-// Clears every lost member from the stored balls and empties the hash slots.
+// Clears every lost member from the stored balls and empties the hash slots.  Also counts,
+// once per round and vertex, the alive edges whose support the round brings up to date
+// (every alive edge at an endpoint of a lost pair).
 __device__ void ph_apply(const LossArgs &a) {
     DevStatus *st = a.st;
-    const int nlost = min(vload(st->nlost), a.lost_max);
+    const int nlost = min(vload(st->nlost), a.lost_max), round = vload(st->round);
+    unsigned long long touched = 0ull;
     for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < 2 * nlost; d += gridDim.x * blockDim.x) {
         const int4 L = a.lost[d >> 1];
         if (L.x < 0) continue;
         const int v = (d & 1) ? L.y : L.x;
         const int w = (d & 1) ? L.x : L.y;
-        const int2 meta = a.ball_meta[v];
-        const int nw = meta.y;
-        const int64_t off = (int64_t)(unsigned)meta.x << 2;
         const uint32_t bit = 1u << (w & 31);
         const uint32_t wi = (uint32_t)(w >> 5);
         uint32_t *word = nullptr;
-        if (nw < 0) {
-            word = a.pool + off + wi;
+        if (a.dense_all) {
+            word = a.pool + (int64_t)v * a.Wpad + wi;
         } else {
-            const uint2 *p = reinterpret_cast<const uint2 *>(a.pool + off);
-            int lo = 0, hi = nw - 1;
-            while (lo <= hi) {
-                const int mid = (lo + hi) >> 1;
-                const uint32_t idx = p[mid].x;
-                if (idx == wi) {
-                    word = a.pool + off + 2 * (int64_t)mid + 1;
-                    break;
+            const int2 meta = a.ball_meta[v];
+            const int nw = meta.y;
+            const int64_t off = (int64_t)(unsigned)meta.x << 2;
+            if (nw < 0) {
+                word = a.pool + off + wi;
+            } else {
+                const uint2 *p = reinterpret_cast<const uint2 *>(a.pool + off);
+                int lo = 0, hi = nw - 1;
+                while (lo <= hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const uint32_t idx = p[mid].x;
+                    if (idx == wi) {
+                        word = a.pool + off + 2 * (int64_t)mid + 1;
+                        break;
+                    }
+                    if (idx < wi) lo = mid + 1;
+                    else hi = mid - 1;
                 }
-                if (idx < wi) lo = mid + 1;
-                else hi = mid - 1;
             }
         }
         if (word) {
@@ -591,13 +638,19 @@ __device__ void ph_apply(const LossArgs &a) {
             if (old & bit) atomicSub(a.ball_size + v, 1);
         }
         if ((d & 1) == 0) a.keys[L.z] = kEmpty;
+        if (atomicExch(a.vtouch + v, round) != round) touched += (unsigned)a.deg_alive[v];
     }
     // lost pairs of this batch (non-null records), one atomic per warp
     unsigned long long real = 0ull;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nlost; r += gridDim.x * blockDim.x)
         real += (a.lost[r].x >= 0);
-    for (int o = 16; o > 0; o >>= 1) real += __shfl_xor_sync(0xffffffffu, real, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        real += __shfl_xor_sync(0xffffffffu, real, o);
+        touched += __shfl_xor_sync(0xffffffffu, touched, o);
+    }
     if ((threadIdx.x & 31) == 0 && real) atomicAdd((unsigned long long *)&st->st_lost, real);
+    if ((threadIdx.x & 31) == 0 && touched)
+        atomicAdd((unsigned long long *)&st->st_recomputed, touched);
 }
 
 // Phase 1 of an incremental round: every alive edge with h-support <= k-2 joins F and is
@@ -682,20 +735,33 @@ __device__ void ph_select_items(const LossArgs &a) {
     }
 }
 
+// Programmatic dependent launch: a phase kernel may be scheduled while the previous one
+// still runs; it waits here until that grid has completed and its writes are visible, then
+// lets the next phase be scheduled in turn.  (Without a programmatic launch the wait
+// returns at once.)
+__device__ __forceinline__ void phase_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // One launch per phase (the rounds of a CUDA graph).
 __global__ void __launch_bounds__(kBlock) k_inc_select(LossArgs a) {
+    phase_entry();
     if (vload(a.st->alive) == 0) return;
     ph_select_items(a);
 }
 __global__ void __launch_bounds__(kBlock) k_loss_detect(LossArgs a) {
+    phase_entry();
     if (vload(a.st->alive) == 0) return;
     ph_detect(a);
 }
 __global__ void __launch_bounds__(kBlock) k_loss_delta(LossArgs a) {
+    phase_entry();
     if (vload(a.st->alive) == 0) return;
     ph_delta(a);
 }
 __global__ void __launch_bounds__(kBlock) k_loss_apply_reduce(LossArgs a) {
+    phase_entry();
     if (vload(a.st->alive) == 0) return;
     ph_apply(a);
     minreduce_body<kBlock / 32>(a.sup, a.m, a.st, 0);
@@ -775,6 +841,8 @@ LossArgs loss_args(Handle *H) {
     a.hub_slot = w.hub_slot;
     a.hub_bits = w.hub_bits;
     a.Wpad = w.Wpad;
+    a.dense_all = w.dense_balls ? 1 : 0;
+    a.hub_all = (w.nhub == g.n && w.hub_min_deg == 1) ? 1 : 0;
     a.m = g.m;
     a.slot_lo = g.slot_lo;
     a.slot_hi = g.slot_hi;
@@ -817,31 +885,78 @@ htd_status launch_persistent_rounds(Handle *H, cudaStream_t s, int max_slots, in
     return HTD_OK;
 }
 
+namespace {
+
+// Blocks of one full wave of a phase kernel (every block resident at once), per device.
+struct PhaseGrids {
+    int device = -1;
+    int detect = 0, delta = 0;
+};
+
+htd_status phase_grids(Handle *H, PhaseGrids &pg) {
+    if (pg.device == H->g.device) return HTD_OK;
+    int od = 0, ou = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, k_loss_detect, kBlock, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_loss_delta, kBlock, 0) != cudaSuccess ||
+        od < 1 || ou < 1) {
+        set_last_error("incremental round: no resident block fits");
+        return HTD_ECUDA;
+    }
+    pg.detect = H->num_sms * od;
+    pg.delta = H->num_sms * ou;
+    pg.device = H->g.device;
+    return HTD_OK;
+}
+
+// One phase launch; `pdl` lets it be scheduled before the previous kernel on the stream
+// has finished (it waits in phase_entry).
+cudaError_t launch_phase(void (*kernel)(LossArgs), int grid, cudaStream_t s, bool pdl,
+                         const LossArgs &a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
+}  // namespace
+
 // Enqueues one incremental round as four launches (the graph path).  evs (nullable):
 // kRoundEvents events; phases are marked as select | - | detect | update | - | reduce.
+// Without events the launches are programmatic (each overlaps the previous one's tail).
 htd_status enqueue_incremental_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t *evs,
                                      unsigned record_flags) {
     LossArgs a = loss_args(H);
-    const int grid = H->num_sms * 8;
+    static thread_local PhaseGrids pg;
+    const htd_status gs = phase_grids(H, pg);
+    if (gs != HTD_OK) return gs;
+    const bool pdl = evs == nullptr;
     auto mark = [&](int i) {
         if (evs) cudaEventRecordWithFlags(evs[i], s, record_flags);
     };
     // the two scans over all edges use fewer blocks: the reduction's per-block atomics all
     // hit the same few counters
     const int grid_scan = H->num_sms * 2;
+    cudaError_t e = cudaSuccess;
     mark(0);
-    k_inc_select<<<grid_scan, kBlock, 0, s>>>(a);
+    if (e == cudaSuccess) e = launch_phase(k_inc_select, grid_scan, s, pdl, a);
     mark(1);
     mark(2);
-    k_loss_detect<<<grid, kBlock, 0, s>>>(a);
+    if (e == cudaSuccess) e = launch_phase(k_loss_detect, pg.detect, s, pdl, a);
     mark(3);
-    k_loss_delta<<<grid, kBlock, 0, s>>>(a);
+    if (e == cudaSuccess) e = launch_phase(k_loss_delta, pg.delta, s, pdl, a);
     mark(4);
     mark(5);
-    k_loss_apply_reduce<<<grid_scan, kBlock, 0, s>>>(a);
+    if (e == cudaSuccess) e = launch_phase(k_loss_apply_reduce, grid_scan, s, pdl, a);
     mark(6);
     *launches += 4;
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_last_error(std::string("enqueue_incremental_round: ") + cudaGetErrorString(e));
         return HTD_ECUDA;

@@ -719,8 +719,9 @@ htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) 
             if (cnt * w.Wpad <= budget_words || T > (1 << 24)) break;
         }
         std::vector<int32_t> slot(n > 0 ? n : 1, -1), list;
+        // T = 1: every vertex gets a set (isolated ones too), so set x sits at row x
         for (int64_t x = 0; x < n; x++)
-            if (rp[x + 1] - rp[x] >= T) {
+            if (T == 1 || rp[x + 1] - rp[x] >= T) {
                 slot[x] = (int32_t)list.size();
                 list.push_back((int32_t)x);
             }

@@ -13,8 +13,9 @@ namespace htd {
 constexpr unsigned kBarrierSpinLimit = 1u << 24;
 
 // Removes edge e at level k in round `round` (Algorithm 1, lines 8-10): t(e) = k, its
-// stamp, a support no selection matches, both adjacency slots marked dead, alive degrees
-// and (when present) the endpoints' alive-adjacency sets updated.
+// stamp, a support no selection matches, both adjacency slots marked dead with the round
+// (-(round + 1), so a slot tells by itself whether it died in the current round), alive
+// degrees and (when present) the endpoints' alive-adjacency sets updated.
 __device__ __forceinline__ void remove_edge(int e, int k, int round, const int32_t *eu,
                                             const int32_t *ev, const int32_t *slot_lo,
                                             const int32_t *slot_hi, int32_t *sup, int32_t *truss,
@@ -24,8 +25,8 @@ __device__ __forceinline__ void remove_edge(int e, int k, int round, const int32
     truss[e] = k;
     stamp[e] = round;
     sup[e] = INT_MAX;
-    col_live[slot_lo[e]] = ~v;
-    col_live[slot_hi[e]] = ~u;
+    col_live[slot_lo[e]] = -(round + 1);
+    col_live[slot_hi[e]] = -(round + 1);
     atomicSub(&deg_alive[u], 1);
     atomicSub(&deg_alive[v], 1);
     if (hub_slot) {

@@ -292,6 +292,21 @@ def test_incremental_matches_rebuild_on_hubby_graph(htd):
         assert torch.equal(a, d) and torch.equal(sa, sd)
 
 
+def test_ball_layout_switch_on_one_handle(htd, oracle_mod):
+    # the captured rounds address the balls by layout: alternating layouts on one handle
+    # must recapture them
+    n = 700
+    s, d = erdos_renyi_gnm(n, 4200, 63)
+    g = gpu_graph(htd, n, s, d)
+    og = oracle_mod.OracleGraph.from_raw(n, s, d)
+    for h in (2, 1):
+        ref = og.truss_decompose(h)[0]
+        for flags in (0, htd.HTD_OPT_COMPACT_BALLS, 0, htd.HTD_OPT_COMPACT_BALLS | htd.HTD_OPT_NO_GRAPH,
+                      htd.HTD_OPT_TIMING, htd.HTD_OPT_COMPACT_BALLS | htd.HTD_OPT_TIMING):
+            t, _, _ = htd.htd_truss_decompose(g, h, flags=flags)
+            np.testing.assert_array_equal(host(t), ref, err_msg=f"h={h} flags={flags}")
+
+
 @pytest.mark.parametrize("h", [1, 2])
 def test_batched_rounds_match_oracle(htd, oracle_mod, h):
     # a 128-slot lost-pair table splits most rounds into many batches
