@@ -253,7 +253,7 @@ def run_gpu(args, world, rank, local):
         classes = [("k_rounds_persistent", mean("ms_round_kernel"), s0["round_kernel_launches"],
                      mean("alg_bytes_detect") + mean("alg_bytes_update") + scan)]
     elif s0["incremental"]:
-        # phase times are sampled (every 8th batch); scale the per-slot mean to all slots
+        # phase times are sampled (every 16th batch); scale the per-slot mean to all slots
         per = slots / timed
         classes = [
             ("k_loss_detect", mean("ms_find") * per, slots, mean("alg_bytes_detect")),
