@@ -165,6 +165,40 @@ htd_status htd_truss_decompose_host(int32_t n, const int32_t *src_host,
                                     int32_t *eu_host, int32_t *ev_host, int32_t *truss_host,
                                     int64_t *m_out, htd_stats *stats, void *stream);
 
+/* Many graphs in one call: every graph's (k,h)-truss decomposition (Def. 4; Sec. 3
+ * peeling), each with its own hop threshold.  The paper decomposes one graph at a time;
+ * the batch relies on the decomposition of a disjoint union being its members'
+ * decompositions (h-support counts only vertices of the edge's own component), so the
+ * graphs of each h are packed, in input order, into disjoint unions of at most
+ * max_union_vertices vertices and each union is peeled once (htd_truss_decompose_ex with
+ * `flags`).  Results are identical to decomposing each graph alone.
+ *   num_graphs        number of graphs (>= 0).
+ *   n, h              host arrays of num_graphs: vertex count (0 <= n <= HTD_MAX_N) and hop
+ *                     threshold (1 <= h <= HTD_MAX_H) of each graph.
+ *   edge_offsets      host array of num_graphs + 1, edge_offsets[0] = 0, non-decreasing:
+ *                     graph g's raw pairs are src_dev/dst_dev[edge_offsets[g] ..
+ *                     edge_offsets[g+1]), ids local to the graph, in [0, n[g]); pairs may
+ *                     repeat, appear reversed or be loops (normalised as htd_build_csr does).
+ *   src_dev, dst_dev  device arrays of edge_offsets[num_graphs] int32.
+ *   max_union_vertices  vertices per union (<= 0: 262,144); a larger graph is a union alone.
+ *   truss_dev         device output with room for edge_offsets[num_graphs] int32.
+ *   out_offsets, out_m  host arrays of num_graphs, filled: graph g's t(e,h) for its
+ *                     canonical edges (htd_edges order of the graph alone) are
+ *                     truss_dev[out_offsets[g] .. out_offsets[g] + out_m[g]).
+ *   num_unions        nullable: receives the number of unions peeled (a union without
+ *                     any pair needs no peel and is not counted).
+ *   stats             nullable: counters summed over the unions (max_truss, h and
+ *                     ball_pool_bytes are maxima; incremental = 1 if every union was).
+ * Synchronous on return.  Errors: EINVAL for a NULL argument, a bad n, h or offset, or an
+ * endpoint outside [0, n[g]) (the message names the graph), EUNSUPPORTED for n > HTD_MAX_N,
+ * EOVERFLOW for a graph with 2*m_in >= 2^31; any error of the underlying calls. */
+htd_status htd_truss_decompose_batched(int32_t num_graphs, const int32_t *n, const int32_t *h,
+                                       const int64_t *edge_offsets, const int32_t *src_dev,
+                                       const int32_t *dst_dev, uint32_t flags,
+                                       int32_t max_union_vertices, int32_t *truss_dev,
+                                       int64_t *out_offsets, int64_t *out_m,
+                                       int32_t *num_unions, htd_stats *stats, void *stream);
+
 /* h-support of every edge without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that must not allocate device memory themselves
  * (code running inside an allocator or memory-pool callback, or under an external budget

@@ -1,0 +1,264 @@
+// htd_batch.cu -- many graphs in one call (htd_truss_decompose_batched).
+//
+// The (k,h)-truss of a disjoint union is the union of the members' (k,h)-trusses: the
+// h-support of an edge counts only vertices of its own component (Def. 2, Def. 3), and the
+// union of edge sets that each satisfy Def. 4 in different components satisfies it too, so
+// t(e,h) in the union equals t(e,h) in e's own graph.  The batch is therefore decomposed as
+// few large disjoint unions: the graphs of one hop threshold h are taken in input order
+// and packed, with their vertex ids shifted, into unions of at most `max_union_vertices`
+// vertices; each union is one peel on the device (every round of it serves all of its
+// members at once).  Because ids are shifted by increasing offsets, the union's canonical
+// (lexicographic) edge order is its members' canonical orders one after the other, so
+// every member's result is a contiguous slice of the union's output.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "htd_internal.h"
+
+namespace htd {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int32_t kDefaultUnionVertices = 1 << 18;
+constexpr int64_t kMaxUnionPairs = ((int64_t)1 << 30) - 1;  // 2 m_in < 2^31
+
+// One member graph of a union: its input pairs [pair_begin, pair_begin + count) land at
+// union pairs [out_begin, out_begin + count), ids shifted by voff and checked against n.
+struct Member {
+    int64_t pair_begin;
+    int64_t out_begin;
+    int64_t count;
+    int32_t voff;
+    int32_t n;
+};
+
+// Copies the members' pairs into the union's arrays with shifted ids.  An id outside
+// [0, n) of its own graph records the smallest such member index in *bad (and the pair
+// becomes a loop, which normalisation drops).
+__global__ void k_union_gather(const Member *__restrict__ mem, int nmem, int64_t total,
+                               const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                               int32_t *__restrict__ usrc, int32_t *__restrict__ udst, int *bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        // the member whose output range holds i (ranges are in increasing order)
+        int lo = 0, hi = nmem - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (mem[mid].out_begin <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const Member M = mem[lo];
+        const int64_t p = M.pair_begin + (i - M.out_begin);
+        int32_t s = src[p], d = dst[p];
+        if (s < 0 || s >= M.n || d < 0 || d >= M.n) {
+            atomicMin(bad, lo);
+            s = 0;
+            d = 0;
+        }
+        usrc[i] = s + M.voff;
+        udst[i] = d + M.voff;
+    }
+}
+
+void add_stats(htd_stats *acc, const htd_stats &s) {
+    acc->rounds += s.rounds;
+    acc->levels += s.levels;
+    acc->max_truss = std::max(acc->max_truss, s.max_truss);
+    acc->h = std::max(acc->h, s.h);
+    acc->hsup_evals += s.hsup_evals;
+    acc->ball_builds += s.ball_builds;
+    acc->balls_changed += s.balls_changed;
+    acc->frontier_edges += s.frontier_edges;
+    acc->pairs_tested += s.pairs_tested;
+    acc->pairs_lost += s.pairs_lost;
+    acc->member_tests += s.member_tests;
+    acc->kernel_launches += s.kernel_launches;
+    acc->ball_pool_bytes = std::max(acc->ball_pool_bytes, s.ball_pool_bytes);
+    acc->timed_slots += s.timed_slots;
+    acc->alg_bytes_ball += s.alg_bytes_ball;
+    acc->alg_bytes_hsup += s.alg_bytes_hsup;
+    acc->alg_bytes_detect += s.alg_bytes_detect;
+    acc->alg_bytes_update += s.alg_bytes_update;
+    acc->ms_initial_ball += s.ms_initial_ball;
+    acc->ms_initial_hsup += s.ms_initial_hsup;
+    acc->ms_select += s.ms_select;
+    acc->ms_find += s.ms_find;
+    acc->ms_remove += s.ms_remove;
+    acc->ms_ball += s.ms_ball;
+    acc->ms_update += s.ms_update;
+    acc->ms_minreduce += s.ms_minreduce;
+    acc->ms_round_kernel += s.ms_round_kernel;
+    acc->round_kernel_launches += s.round_kernel_launches;
+    acc->slots += s.slots;
+}
+
+// Frees the union's scratch on every exit path.
+struct UnionScratch {
+    Member *mem = nullptr;
+    int32_t *usrc = nullptr, *udst = nullptr;
+    int *bad = nullptr;
+    htd_graph *g = nullptr;
+    ~UnionScratch() {
+        if (g) htd_graph_free(g);
+        cudaFree(mem);
+        cudaFree(usrc);
+        cudaFree(udst);
+        cudaFree(bad);
+    }
+};
+
+}  // namespace
+}  // namespace htd
+
+extern "C" htd_status htd_truss_decompose_batched(
+    int32_t num_graphs, const int32_t *n, const int32_t *h, const int64_t *edge_offsets,
+    const int32_t *src_dev, const int32_t *dst_dev, uint32_t flags, int32_t max_union_vertices,
+    int32_t *truss_dev, int64_t *out_offsets, int64_t *out_m, int32_t *num_unions,
+    htd_stats *stats, void *stream) {
+    using namespace htd;
+    if (num_graphs < 0 || (num_graphs > 0 && (!n || !h || !edge_offsets || !out_offsets || !out_m))) {
+        set_last_error("htd_truss_decompose_batched: NULL argument or num_graphs < 0");
+        return HTD_EINVAL;
+    }
+    if (num_graphs > 0 && edge_offsets[0] != 0) {
+        set_last_error("htd_truss_decompose_batched: edge_offsets[0] must be 0");
+        return HTD_EINVAL;
+    }
+    for (int32_t g = 0; g < num_graphs; g++) {
+        if (n[g] < 0 || h[g] < 1 || h[g] > HTD_MAX_H || edge_offsets[g + 1] < edge_offsets[g]) {
+            set_last_error("htd_truss_decompose_batched: graph " + std::to_string(g) +
+                           ": n < 0, h outside [1, HTD_MAX_H] or decreasing edge_offsets");
+            return HTD_EINVAL;
+        }
+        if (n[g] > HTD_MAX_N) {
+            set_last_error("htd_truss_decompose_batched: graph " + std::to_string(g) +
+                           ": n exceeds HTD_MAX_N");
+            return HTD_EUNSUPPORTED;
+        }
+        if (edge_offsets[g + 1] - edge_offsets[g] > kMaxUnionPairs) {
+            set_last_error("htd_truss_decompose_batched: graph " + std::to_string(g) +
+                           ": 2*m_in >= 2^31");
+            return HTD_EOVERFLOW;
+        }
+    }
+    const int64_t total_in = num_graphs > 0 ? edge_offsets[num_graphs] : 0;
+    if (total_in > 0 && (!src_dev || !dst_dev || !truss_dev)) {
+        set_last_error("htd_truss_decompose_batched: NULL device buffer");
+        return HTD_EINVAL;
+    }
+    const int32_t cap_n = max_union_vertices > 0 ? std::min<int32_t>(max_union_vertices, HTD_MAX_N)
+                                                 : kDefaultUnionVertices;
+    htd_stats acc;
+    std::memset(&acc, 0, sizeof(acc));
+    acc.incremental = 1;
+    int32_t unions = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t out_pos = 0;
+
+    // graphs of each h in input order, packed greedily into unions
+    std::vector<int32_t> order;
+    for (int32_t hh = 1; hh <= HTD_MAX_H; hh++)
+        for (int32_t g = 0; g < num_graphs; g++)
+            if (h[g] == hh) order.push_back(g);
+    size_t i = 0;
+    while (i < order.size()) {
+        const int32_t hh = h[order[i]];
+        std::vector<Member> mem;
+        std::vector<int32_t> ids;
+        int64_t nu = 0, pairs = 0;
+        while (i < order.size() && h[order[i]] == hh) {
+            const int32_t g = order[i];
+            const int64_t cnt = edge_offsets[g + 1] - edge_offsets[g];
+            if (!mem.empty() && (nu + n[g] > cap_n || pairs + cnt > kMaxUnionPairs)) break;
+            mem.push_back(Member{edge_offsets[g], pairs, cnt, (int32_t)nu, n[g]});
+            ids.push_back(g);
+            nu += n[g];
+            pairs += cnt;
+            i++;
+        }
+        if (pairs == 0) {  // no pairs at all: every member has zero edges
+            for (size_t j = 0; j < mem.size(); j++) {
+                out_offsets[ids[j]] = out_pos;
+                out_m[ids[j]] = 0;
+            }
+            continue;
+        }
+        UnionScratch U;
+        cudaError_t e = cudaSuccess;
+        {
+            e = cudaMalloc(&U.mem, mem.size() * sizeof(Member));
+            if (e == cudaSuccess) e = cudaMalloc(&U.usrc, pairs * sizeof(int32_t));
+            if (e == cudaSuccess) e = cudaMalloc(&U.udst, pairs * sizeof(int32_t));
+            if (e == cudaSuccess) e = cudaMalloc(&U.bad, sizeof(int));
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(U.mem, mem.data(), mem.size() * sizeof(Member),
+                                    cudaMemcpyHostToDevice, s);
+            const int none = INT32_MAX;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(U.bad, &none, sizeof(int), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) {
+                const int64_t blocks = std::min<int64_t>((pairs + kBlock - 1) / kBlock, 4096);
+                k_union_gather<<<(unsigned)blocks, kBlock, 0, s>>>(U.mem, (int)mem.size(), pairs, src_dev,
+                                                                  dst_dev, U.usrc, U.udst, U.bad);
+                add_launches(1);
+                e = cudaGetLastError();
+            }
+            int bad = INT32_MAX;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, U.bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                set_last_error(std::string("htd_truss_decompose_batched: ") + cudaGetErrorString(e));
+                return e == cudaErrorMemoryAllocation ? HTD_ENOMEM : HTD_ECUDA;
+            }
+            if (bad != INT32_MAX) {
+                set_last_error("htd_truss_decompose_batched: graph " + std::to_string(ids[bad]) +
+                               ": an endpoint outside [0, n)");
+                return HTD_EINVAL;
+            }
+        }
+        htd_status st = htd_build_csr((int32_t)nu, U.usrc, U.udst, pairs, 1, stream, &U.g);
+        if (st != HTD_OK) return st;
+        int32_t nn = 0;
+        int64_t mu = 0;
+        htd_graph_info(U.g, &nn, &mu);
+        htd_stats us;
+        std::memset(&us, 0, sizeof(us));
+        st = htd_truss_decompose_ex(U.g, hh, flags, truss_dev + out_pos, nullptr, &us, stream);
+        if (st != HTD_OK) return st;
+        add_stats(&acc, us);
+        if (!us.incremental) acc.incremental = 0;
+        // member g's edges: the canonical edges whose smaller endpoint lies in its id range
+        std::vector<int32_t> eu(mu > 0 ? mu : 1);
+        if (mu > 0) {
+            int32_t *eu_dev = nullptr, *ev_dev = nullptr;
+            e = cudaMalloc(&eu_dev, mu * sizeof(int32_t));
+            if (e == cudaSuccess) e = cudaMalloc(&ev_dev, mu * sizeof(int32_t));
+            if (e == cudaSuccess) {
+                st = htd_edges(U.g, eu_dev, ev_dev, stream);
+                if (st == HTD_OK)
+                    e = cudaMemcpyAsync(eu.data(), eu_dev, mu * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+                if (st == HTD_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
+            }
+            cudaFree(eu_dev);
+            cudaFree(ev_dev);
+            if (st != HTD_OK) return st;
+            if (e != cudaSuccess) {
+                set_last_error(std::string("htd_truss_decompose_batched: ") + cudaGetErrorString(e));
+                return e == cudaErrorMemoryAllocation ? HTD_ENOMEM : HTD_ECUDA;
+            }
+        }
+        for (size_t j = 0; j < mem.size(); j++) {
+            const int32_t lo_id = mem[j].voff, hi_id = mem[j].voff + mem[j].n;
+            const int64_t b = std::lower_bound(eu.begin(), eu.begin() + mu, lo_id) - eu.begin();
+            const int64_t t = std::lower_bound(eu.begin(), eu.begin() + mu, hi_id) - eu.begin();
+            out_offsets[ids[j]] = out_pos + b;
+            out_m[ids[j]] = t - b;
+        }
+        out_pos += mu;
+        unions++;
+    }
+    if (num_unions) *num_unions = unions;
+    if (stats) *stats = acc;
+    return HTD_OK;
+}

@@ -97,6 +97,8 @@ struct Handle {
 };
 
 void set_last_error(const std::string &msg);
+// Adds kernels launched outside the handle calls to the thread's launch counter.
+void add_launches(int64_t k);
 
 // CSR builder (htd_csr.cu).  src/dst are device pointers.
 htd_status build_csr_device(int32_t n, const int32_t *src, const int32_t *dst, int64_t m_in,

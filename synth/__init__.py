@@ -10,6 +10,7 @@ from .generators import (  # noqa: F401
     CONFIG_SEED_BASE,
     GraphSpec,
     barabasi_albert,
+    batch_graphs,
     config_graph,
     dcsbm,
     erdos_renyi_gnm,

@@ -13,6 +13,8 @@ Workloads (sizes follow the paper's datasets, Table 1, by shape):
                      Stands in for the Amazon TWEB graph (262,111 vertices).
 * ``dcsbm_n200k`` -- degree-corrected SBM, 200 power-law blocks, mean degree 12,
                      10% inter-block edges.  Stands in for the Amazon MDS graph.
+* ``batch_graphs`` -- many small ER / BA graphs with mixed h (the batched form; 4,096
+                     graphs of 50..5,000 vertices at seed 0x48545258 for the benchmark).
 """
 
 from __future__ import annotations
@@ -248,6 +250,28 @@ def config_graph(name: str) -> GraphSpec:
         return GraphSpec(name, 1 << scale, s, d, (2,),
                          f"R-MAT scale {scale}, edge factor 8, (0.57,0.19,0.19,0.05)")
     raise KeyError(name)
+
+
+def batch_graphs(count: int, seed: int, n_lo: int = 50, n_hi: int = 5000):
+    """A batch of small graphs: per graph n ~ U[n_lo, n_hi], either Erdos-Renyi with mean
+    degree 8 (M = 4n distinct pairs) or Barabasi-Albert with m0 ~ U{2..8}, and a hop
+    threshold h ~ U{2,3}.  Graph i draws its edges from sub-seed seed ^ i.  Returns a list
+    of (n, src, dst, h)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        sub = seed ^ i
+        n = int(rng.integers(n_lo, n_hi + 1))
+        h = int(rng.integers(2, 4))
+        if rng.random() < 0.5:
+            m = min(4 * n, n * (n - 1) // 2)
+            s, d = erdos_renyi_gnm(n, m, sub)
+        else:
+            m0 = int(rng.integers(2, 9))
+            n = max(n, m0 + 1)
+            s, d = barabasi_albert(n, m0, sub)
+        out.append((n, s, d, h))
+    return out
 
 
 def small_corpus(count: int, seed: int, max_n: int = 40):

@@ -70,6 +70,33 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.htd_truss_decompose(None, 2, None, None, None, None) == 1
 
 
+def test_batched_arguments_rejected_on_host(lib):
+    import numpy as np
+
+    def call(n, h, off, num=None):
+        n = np.asarray(n, dtype=np.int32)
+        h = np.asarray(h, dtype=np.int32)
+        off = np.asarray(off, dtype=np.int64)
+        k = len(n) if num is None else num
+        oo = np.zeros(max(len(n), 1), dtype=np.int64)
+        om = np.zeros(max(len(n), 1), dtype=np.int64)
+        vp = lambda a: ctypes.c_void_p(a.ctypes.data)
+        return lib.htd_truss_decompose_batched(k, vp(n), vp(h), vp(off), None, None, 0, 0, None,
+                                               vp(oo), vp(om), None, None, None)
+
+    assert call([4], [2], [0, 0], num=-1) == 1          # negative count
+    assert call([4], [0], [0, 0]) == 1                  # h below 1
+    assert call([4], [9], [0, 0]) == 1                  # h above HTD_MAX_H
+    assert call([-1], [2], [0, 0]) == 1                 # negative n
+    assert call([4, 4], [2, 2], [0, 3, 1]) == 1         # decreasing offsets
+    assert call([4], [2], [1, 3]) == 1                  # offsets not starting at 0
+    assert call([2_000_000], [2], [0, 0]) == 6          # n above HTD_MAX_N
+    assert call([4], [2], [0, 2]) == 1                  # pairs but NULL device buffers
+    assert call([4], [2], [0, 1 << 31]) == 5            # 2 m_in >= 2^31
+    assert lib.htd_truss_decompose_batched(0, None, None, None, None, None, 0, 0, None, None,
+                                           None, None, None, None) == 0  # empty batch
+
+
 def test_no_cpu_fallback_without_a_gpu(lib):
     import torch
 
