@@ -114,6 +114,23 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(value: float, world: int, device="cpu") -> float:
+    """The largest value over all ranks (a replicated job takes as long as its slowest
+    rank).  One all-reduce on the process group; with one rank, the value itself."""
+    if world <= 1:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_replica: int, steps: int, t_max_ms: float, world: int) -> float:
+    """Units all replicas processed per second of the slowest rank's time."""
+    return world * units_per_replica * steps / (t_max_ms / 1e3)
+
+
 def oracle_sample(budget_s: float, h: int):
     """The CPU oracle, as it stands, on down-scaled R-MAT graphs with the workload's
     generator parameters: scales grow until the cumulative time passes the budget.
@@ -209,13 +226,9 @@ def run_gpu(args, world, rank, local):
         torch.cuda.synchronize()
     launches = lib.htd_kernel_launch_count() - launches0
     ms = [a.elapsed_time(b) for a, b in ev]
-    t_max = float(np.sum(ms))
-    if world > 1:
-        tt = torch.tensor([t_max], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(float(np.sum(ms)), world, dev)
     ms_step = t_max / args.steps
-    value = world * m * args.steps / (t_max / 1e3)
+    value = job_throughput(m, args.steps, t_max, world)
 
     # end to end through the host-buffer entry point (pinned buffers, copies inside)
     e2e_value, e2e_ms = None, []
