@@ -73,6 +73,8 @@ def _load():
         lib.htdo_certify.restype = i64
         lib.htdo_check_stamp_order.argtypes = [i64, p, p]
         lib.htdo_check_stamp_order.restype = i64
+        lib.htdo_hindex.argtypes = [p, i32, i32, i32, p, p]
+        lib.htdo_hindex.restype = i32
         _lib = lib
         return lib
 
@@ -148,6 +150,17 @@ class OracleGraph:
         if self._lib.htdo_truss_sequential(self._g, int(h), _ptr(t)) != 0:
             raise MemoryError("oracle sequential peel: allocation failed")
         return t[: self.m]
+
+    def hindex(self, h: int, asynchronous: bool = False, max_iter: int = -1):
+        """The H-index iteration of Sec. 4 from H^(0) = sup(e,h).  Returns (H values after
+        the last order computed, orders computed, converged).  Converged: t = H + 2."""
+        hv = np.zeros(max(1, self.m), dtype=np.int32)
+        it = ctypes.c_int32()
+        rc = self._lib.htdo_hindex(self._g, int(h), int(bool(asynchronous)), int(max_iter),
+                                   _ptr(hv), ctypes.byref(it))
+        if rc < 0:
+            raise MemoryError("oracle H-index iteration: allocation failed")
+        return hv[: self.m], int(it.value), rc == 1
 
     def certify(self, h: int, t, stamp, edges=None):
         """Peeling certificate: returns (stamp_order_violations, failing_edges, fail_codes).

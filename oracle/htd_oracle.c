@@ -310,3 +310,131 @@ int64_t htdo_check_stamp_order(int64_t m, const int32_t *t, const int32_t *stamp
     free(tmin); free(tmax);
     return bad;
 }
+
+/* ---- The H-index iteration of Sec. 4 (Definition of the h-hop reachable path key,
+ * Theorems 3 and 4, Algorithm 2; asynchronous updating) ------------------------------
+ *
+ * H(S) is the H-index of a multiset S: the largest y such that at least y members of S
+ * are >= y.  With H^(0)(e) = sup_G(e,h), order n computes for e = (u,v)
+ *     H^(n)(e) = H({ min(P(u,w), P(v,w)) : w in N_G(u,h) ∩ N_G(v,h) }),
+ * where P(a,b), the h-hop reachable path key, is the largest over paths from a to b of at
+ * most h edges of the smallest H^(n-1) on the path.  Readings: the paths have at most h
+ * edges (with unbounded paths the proof of Theorem 4 (ii) does not hold), they may use e
+ * itself, and the common h-neighbourhood is that of the whole graph G.  The iteration
+ * stops at the first order n with H^(n) = H^(n-1) on every edge; t(e,h) = H^(n)(e) + 2
+ * (Theorem 4).  Asynchronous updating (Sec. 4) takes the edges in id order and uses every
+ * value already updated in the current sweep. */
+
+/* H-index of vals[0..cnt) (reorders vals). */
+static int32_t h_index(int32_t *vals, int64_t cnt) {
+    /* counting by value: c[y] = members equal to y, capped at cnt */
+    int64_t *c = (int64_t *)calloc((size_t)cnt + 2, sizeof(int64_t));
+    if (!c) return -1;
+    for (int64_t i = 0; i < cnt; i++) {
+        int64_t v = vals[i] < 0 ? 0 : vals[i];
+        c[v > cnt ? cnt : v]++;
+    }
+    int64_t at_least = 0;
+    int32_t y = 0;
+    for (int64_t v = cnt; v >= 0; v--) {
+        at_least += c[v];
+        if (at_least >= v) { y = (int32_t)v; break; }
+    }
+    free(c);
+    return y;
+}
+
+/* P(src, w) for every vertex w: hop-limited widest paths by h rounds of relaxation over
+ * all edges (round r extends the paths of at most r-1 edges by one edge).  key = H per
+ * edge.  best[w] = -1 where no path of at most h edges exists; best[src] = INT32_MAX (the
+ * empty path). */
+static void path_keys(const htdo_graph *g, int32_t src, int32_t h, const int32_t *key,
+                      int32_t *best, int32_t *prev) {
+    for (int32_t x = 0; x < g->n; x++) best[x] = -1;
+    best[src] = INT32_MAX;
+    for (int32_t r = 1; r <= h; r++) {
+        memcpy(prev, best, (size_t)g->n * sizeof(int32_t));
+        for (int64_t e = 0; e < g->m; e++) {
+            int32_t a = g->eu[e], b = g->ev[e];
+            if (prev[a] >= 0) {
+                int32_t c = prev[a] < key[e] ? prev[a] : key[e];
+                if (c > best[b]) best[b] = c;
+            }
+            if (prev[b] >= 0) {
+                int32_t c = prev[b] < key[e] ? prev[b] : key[e];
+                if (c > best[a]) best[a] = c;
+            }
+        }
+    }
+}
+
+/* One order of the iteration for edge e from the keys `key`: H({min(P(u,w),P(v,w))}). */
+static int32_t hindex_edge(htdo_graph *g, int32_t h, const int32_t *key, int64_t e,
+                           int32_t *pu, int32_t *pv, int32_t *tmp, int32_t *vals) {
+    int32_t u = g->eu[e], v = g->ev[e];
+    path_keys(g, u, h, key, pu, tmp);
+    path_keys(g, v, h, key, pv, tmp);
+    /* the common h-neighbours of e in G */
+    int64_t na = ball_bfs(g, u, h, NULL, 0, g->dist_a, g->queue_a);
+    int64_t nb = ball_bfs(g, v, h, NULL, 0, g->dist_b, g->queue_b);
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < na; i++) {
+        int32_t w = g->queue_a[i];
+        if (w == u || w == v || g->dist_b[w] < 0) continue;
+        vals[cnt++] = pu[w] < pv[w] ? pu[w] : pv[w];
+    }
+    ball_reset(g->dist_a, g->queue_a, na);
+    ball_reset(g->dist_b, g->queue_b, nb);
+    return h_index(vals, cnt);
+}
+
+/* The H-index iteration from H^(0) = sup_G(e,h) for at most max_iter orders (max_iter < 0:
+ * until stable).  asynchronous = 0: order n uses only H^(n-1) (Algorithm 2);
+ * asynchronous = 1: Gauss-Seidel sweeps in edge id order.  hv_out receives the last H
+ * values; iters_out the orders computed (the last one changed nothing when converged).
+ * Returns 1 if converged, 0 if stopped at max_iter (or, which Theorem 3 rules out, after
+ * more orders than the values can decrease), -1 on allocation failure. */
+int32_t htdo_hindex(htdo_graph *g, int32_t h, int32_t asynchronous, int32_t max_iter,
+                    int32_t *hv_out, int32_t *iters_out) {
+    int64_t m = g->m;
+    size_t mm = (size_t)(m > 0 ? m : 1), nn = (size_t)(g->n > 0 ? g->n : 1);
+    int32_t *cur = (int32_t *)malloc(mm * sizeof(int32_t));
+    int32_t *nxt = (int32_t *)malloc(mm * sizeof(int32_t));
+    int32_t *pu = (int32_t *)malloc(nn * sizeof(int32_t));
+    int32_t *pv = (int32_t *)malloc(nn * sizeof(int32_t));
+    int32_t *tmp = (int32_t *)malloc(nn * sizeof(int32_t));
+    int32_t *vals = (int32_t *)malloc(nn * sizeof(int32_t));
+    int32_t rc = 0, n = 0;
+    if (!cur || !nxt || !pu || !pv || !tmp || !vals) { rc = -1; goto done; }
+    htdo_h_support(g, h, NULL, 0, cur);
+    /* every order before the fixed point lowers at least one value by at least one
+     * (Theorem 3), so 1 + sum of H^(0) orders always suffice */
+    int64_t cap = 1;
+    for (int64_t e = 0; e < m; e++) cap += cur[e];
+    for (;;) {
+        if (max_iter >= 0 && n >= max_iter) break;
+        if (n >= cap) break;
+        int changed = 0;
+        if (asynchronous) {
+            for (int64_t e = 0; e < m; e++) {
+                int32_t v = hindex_edge(g, h, cur, e, pu, pv, tmp, vals);
+                if (v < 0) { rc = -1; goto done; }
+                if (v != cur[e]) { cur[e] = v; changed = 1; }
+            }
+        } else {
+            for (int64_t e = 0; e < m; e++) {
+                nxt[e] = hindex_edge(g, h, cur, e, pu, pv, tmp, vals);
+                if (nxt[e] < 0) { rc = -1; goto done; }
+                if (nxt[e] != cur[e]) changed = 1;
+            }
+            int32_t *t = cur; cur = nxt; nxt = t;
+        }
+        n++;
+        if (!changed) { rc = 1; break; }
+    }
+    if (m > 0) memcpy(hv_out, cur, (size_t)m * sizeof(int32_t));
+done:
+    if (iters_out) *iters_out = n;
+    free(cur); free(nxt); free(pu); free(pv); free(tmp); free(vals);
+    return rc;
+}

@@ -122,6 +122,34 @@ def classic_truss(n, edges):
     return t
 
 
+def triangle_hindex_orders(n, edges, orders):
+    """Classic H-index iteration for the k-truss (h = 1): order 0 is every edge's triangle
+    count; order k+1 of e is the H-index of {min(H_k(e1), H_k(e2))} over the triangle edge
+    pairs (e1, e2) of e.  Returns the value arrays of orders 0..orders."""
+    adj = [set() for _ in range(n)]
+    for u, v in edges:
+        adj[u].add(v)
+        adj[v].add(u)
+    eid = {e: i for i, e in enumerate(edges)}
+    pairs = []
+    for u, v in edges:
+        pairs.append([(eid[(min(u, w), max(u, w))], eid[(min(v, w), max(v, w))])
+                      for w in sorted(adj[u] & adj[v])])
+    cur = np.array([len(p) for p in pairs], dtype=np.int64)
+    out = [cur.copy()]
+    for _ in range(orders):
+        nxt = np.zeros_like(cur)
+        for i, p in enumerate(pairs):
+            vals = sorted((min(cur[a], cur[b]) for a, b in p), reverse=True)
+            y = 0
+            while y < len(vals) and vals[y] >= y + 1:
+                y += 1
+            nxt[i] = y
+        cur = nxt
+        out.append(cur.copy())
+    return out
+
+
 # ---- closed-form families -------------------------------------------------------------
 
 def complete(n):

@@ -271,3 +271,62 @@ def test_oracle_finishes_small_workload_quickly(oracle_mod):
     g = oracle_mod.OracleGraph.from_raw(500, s, d)
     t, stamp, rounds = g.truss_decompose(2)
     assert rounds > 0 and (t >= 2).all()
+
+
+# ---- the H-index iteration of Sec. 4 (Theorems 3 and 4; asynchronous updating) -----------
+
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_hindex_converges_to_definition(oracle_mod, h):
+    # Theorem 4: the fixed point plus 2 is t(e,h), here against Def. 4 by brute force
+    for seed in range(20):
+        n, edges = random_small(6000 + 13 * h + seed, n_max=7, m_max=10)
+        g = og(oracle_mod, n, edges)
+        ref = pins.truss_by_definition(n, edges, h)
+        for asynchronous in (False, True):
+            hv, _, converged = g.hindex(h, asynchronous=asynchronous)
+            assert converged
+            np.testing.assert_array_equal(hv + 2, ref)
+
+
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_hindex_fixed_point_equals_peeling_on_corpus(oracle_mod, h):
+    for n, s, d in small_corpus(24, 900 + h, max_n=30):
+        g = oracle_mod.OracleGraph.from_raw(n, s, d)
+        t = g.truss_decompose(h)[0]
+        for asynchronous in (False, True):
+            hv, _, converged = g.hindex(h, asynchronous=asynchronous)
+            assert converged
+            np.testing.assert_array_equal(hv + 2, t)
+
+
+def test_hindex_orders_monotone_and_bounded(oracle_mod):
+    # order 0 is the h-support; orders never increase (Theorem 3) and never fall below
+    # t(e,h) - 2 (Theorem 4 (i))
+    for h in (1, 2, 3):
+        for seed in range(4):
+            s, d = erdos_renyi_gnm(25, 70, 7100 + 10 * h + seed)
+            g = oracle_mod.OracleGraph.from_raw(25, s, d)
+            t = g.truss_decompose(h)[0]
+            _, final, _ = g.hindex(h)
+            prev = None
+            for k in range(final + 1):
+                hv, _, _ = g.hindex(h, max_iter=k)
+                if k == 0:
+                    np.testing.assert_array_equal(hv, g.h_support(h))
+                else:
+                    assert np.all(hv <= prev)
+                assert np.all(hv >= t - 2)
+                prev = hv
+
+
+def test_hindex_h1_is_the_triangle_hindex(oracle_mod):
+    # h = 1: the only path of at most one edge is the edge itself, so each order is the
+    # classic triangle-pair H-index, order by order
+    for seed in range(6):
+        s, d = erdos_renyi_gnm(30, 110, 7300 + seed)
+        g = oracle_mod.OracleGraph.from_raw(30, s, d)
+        edges = list(zip(g.eu.tolist(), g.ev.tolist()))
+        ref = pins.triangle_hindex_orders(30, edges, 6)
+        for k in range(7):
+            hv, _, _ = g.hindex(1, max_iter=k)
+            np.testing.assert_array_equal(hv, ref[k], err_msg=f"order {k}")
