@@ -199,6 +199,19 @@ htd_status htd_truss_decompose_batched(int32_t num_graphs, const int32_t *n, con
                                        int64_t *out_offsets, int64_t *out_m,
                                        int32_t *num_unions, htd_stats *stats, void *stream);
 
+/* The union packing htd_truss_decompose_batched uses, computed on the host only (no
+ * device call): graphs are taken by increasing h and, within one h, in input order; a
+ * union is closed when the next graph would take it past max_union_vertices vertices (<=
+ * 0: 262,144) or 2^30 - 1 raw pairs; a larger graph forms a union alone.
+ *   union_of, vertex_offset  host arrays of num_graphs, filled: the union of graph g
+ *                            (numbered in the order they are peeled, unions without any
+ *                            pair included) and the shift added to its vertex ids there.
+ *   num_unions               nullable: receives the number of unions.
+ * Same argument checks and errors as htd_truss_decompose_batched (no device buffers). */
+htd_status htd_batch_plan(int32_t num_graphs, const int32_t *n, const int32_t *h,
+                          const int64_t *edge_offsets, int32_t max_union_vertices,
+                          int32_t *union_of, int32_t *vertex_offset, int32_t *num_unions);
+
 /* h-support of every edge without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that must not allocate device memory themselves
  * (code running inside an allocator or memory-pool callback, or under an external budget

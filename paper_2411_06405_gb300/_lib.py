@@ -31,7 +31,7 @@ EXPORTED = (
     "htd_build_csr", "htd_graph_info", "htd_edges", "htd_csr", "htd_h_support",
     "htd_truss_decompose", "htd_truss_decompose_ex", "htd_truss_decompose_host",
     "htd_graph_free", "htd_kernel_launch_count", "htd_status_string", "htd_last_error",
-    "htd_h_support_static", "htd_truss_decompose_batched",
+    "htd_h_support_static", "htd_truss_decompose_batched", "htd_batch_plan",
 )
 
 
@@ -113,6 +113,7 @@ def load():
             "htd_h_support_static": ([i32, p, p, i64, p, p, i32, p, p], ctypes.c_int),
             "htd_truss_decompose_batched": ([i32, p, p, p, p, p, u32, i32, p, p, p,
                                              ctypes.POINTER(i32), ps, p], ctypes.c_int),
+            "htd_batch_plan": ([i32, p, p, p, i32, p, p, ctypes.POINTER(i32)], ctypes.c_int),
             "htd_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "htd_last_error": ([], ctypes.c_char_p),
         }

@@ -94,6 +94,65 @@ void add_stats(htd_stats *acc, const htd_stats &s) {
     acc->slots += s.slots;
 }
 
+// One union of the plan: its hop threshold and members (graph ids, in input order).
+struct UnionPlan {
+    int32_t h;
+    std::vector<Member> mem;
+    std::vector<int32_t> ids;
+    int64_t n;      // vertices
+    int64_t pairs;  // raw pairs
+};
+
+// Checks the batch description and packs it: graphs of each h in input order, a new
+// union whenever the next graph would take it past cap_n vertices or 2^30 - 1 pairs (a
+// graph larger than cap_n forms a union alone).
+htd_status plan_unions(const char *who, int32_t num_graphs, const int32_t *n, const int32_t *h,
+                       const int64_t *edge_offsets, int32_t max_union_vertices,
+                       std::vector<UnionPlan> *plan) {
+    if (num_graphs < 0 || (num_graphs > 0 && (!n || !h || !edge_offsets))) {
+        set_last_error(std::string(who) + ": NULL argument or num_graphs < 0");
+        return HTD_EINVAL;
+    }
+    if (num_graphs > 0 && edge_offsets[0] != 0) {
+        set_last_error(std::string(who) + ": edge_offsets[0] must be 0");
+        return HTD_EINVAL;
+    }
+    for (int32_t g = 0; g < num_graphs; g++) {
+        if (n[g] < 0 || h[g] < 1 || h[g] > HTD_MAX_H || edge_offsets[g + 1] < edge_offsets[g]) {
+            set_last_error(std::string(who) + ": graph " + std::to_string(g) +
+                           ": n < 0, h outside [1, HTD_MAX_H] or decreasing edge_offsets");
+            return HTD_EINVAL;
+        }
+        if (n[g] > HTD_MAX_N) {
+            set_last_error(std::string(who) + ": graph " + std::to_string(g) + ": n exceeds HTD_MAX_N");
+            return HTD_EUNSUPPORTED;
+        }
+        if (edge_offsets[g + 1] - edge_offsets[g] > kMaxUnionPairs) {
+            set_last_error(std::string(who) + ": graph " + std::to_string(g) + ": 2*m_in >= 2^31");
+            return HTD_EOVERFLOW;
+        }
+    }
+    const int32_t cap_n = max_union_vertices > 0 ? std::min<int32_t>(max_union_vertices, HTD_MAX_N)
+                                                 : kDefaultUnionVertices;
+    plan->clear();
+    for (int32_t hh = 1; hh <= HTD_MAX_H; hh++) {
+        for (int32_t g = 0; g < num_graphs; g++) {
+            if (h[g] != hh) continue;
+            const int64_t cnt = edge_offsets[g + 1] - edge_offsets[g];
+            if (plan->empty() || plan->back().h != hh || plan->back().n + n[g] > cap_n ||
+                plan->back().pairs + cnt > kMaxUnionPairs) {
+                plan->push_back(UnionPlan{hh, {}, {}, 0, 0});
+            }
+            UnionPlan &u = plan->back();
+            u.mem.push_back(Member{edge_offsets[g], u.pairs, cnt, (int32_t)u.n, n[g]});
+            u.ids.push_back(g);
+            u.n += n[g];
+            u.pairs += cnt;
+        }
+    }
+    return HTD_OK;
+}
+
 // Frees the union's scratch on every exit path.
 struct UnionScratch {
     Member *mem = nullptr;
@@ -118,38 +177,19 @@ extern "C" htd_status htd_truss_decompose_batched(
     int32_t *truss_dev, int64_t *out_offsets, int64_t *out_m, int32_t *num_unions,
     htd_stats *stats, void *stream) {
     using namespace htd;
-    if (num_graphs < 0 || (num_graphs > 0 && (!n || !h || !edge_offsets || !out_offsets || !out_m))) {
-        set_last_error("htd_truss_decompose_batched: NULL argument or num_graphs < 0");
+    std::vector<UnionPlan> plan;
+    const htd_status ps = plan_unions("htd_truss_decompose_batched", num_graphs, n, h, edge_offsets,
+                                      max_union_vertices, &plan);
+    if (ps != HTD_OK) return ps;
+    if (num_graphs > 0 && (!out_offsets || !out_m)) {
+        set_last_error("htd_truss_decompose_batched: NULL output array");
         return HTD_EINVAL;
-    }
-    if (num_graphs > 0 && edge_offsets[0] != 0) {
-        set_last_error("htd_truss_decompose_batched: edge_offsets[0] must be 0");
-        return HTD_EINVAL;
-    }
-    for (int32_t g = 0; g < num_graphs; g++) {
-        if (n[g] < 0 || h[g] < 1 || h[g] > HTD_MAX_H || edge_offsets[g + 1] < edge_offsets[g]) {
-            set_last_error("htd_truss_decompose_batched: graph " + std::to_string(g) +
-                           ": n < 0, h outside [1, HTD_MAX_H] or decreasing edge_offsets");
-            return HTD_EINVAL;
-        }
-        if (n[g] > HTD_MAX_N) {
-            set_last_error("htd_truss_decompose_batched: graph " + std::to_string(g) +
-                           ": n exceeds HTD_MAX_N");
-            return HTD_EUNSUPPORTED;
-        }
-        if (edge_offsets[g + 1] - edge_offsets[g] > kMaxUnionPairs) {
-            set_last_error("htd_truss_decompose_batched: graph " + std::to_string(g) +
-                           ": 2*m_in >= 2^31");
-            return HTD_EOVERFLOW;
-        }
     }
     const int64_t total_in = num_graphs > 0 ? edge_offsets[num_graphs] : 0;
     if (total_in > 0 && (!src_dev || !dst_dev || !truss_dev)) {
         set_last_error("htd_truss_decompose_batched: NULL device buffer");
         return HTD_EINVAL;
     }
-    const int32_t cap_n = max_union_vertices > 0 ? std::min<int32_t>(max_union_vertices, HTD_MAX_N)
-                                                 : kDefaultUnionVertices;
     htd_stats acc;
     std::memset(&acc, 0, sizeof(acc));
     acc.incremental = 1;
@@ -157,27 +197,11 @@ extern "C" htd_status htd_truss_decompose_batched(
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int64_t out_pos = 0;
 
-    // graphs of each h in input order, packed greedily into unions
-    std::vector<int32_t> order;
-    for (int32_t hh = 1; hh <= HTD_MAX_H; hh++)
-        for (int32_t g = 0; g < num_graphs; g++)
-            if (h[g] == hh) order.push_back(g);
-    size_t i = 0;
-    while (i < order.size()) {
-        const int32_t hh = h[order[i]];
-        std::vector<Member> mem;
-        std::vector<int32_t> ids;
-        int64_t nu = 0, pairs = 0;
-        while (i < order.size() && h[order[i]] == hh) {
-            const int32_t g = order[i];
-            const int64_t cnt = edge_offsets[g + 1] - edge_offsets[g];
-            if (!mem.empty() && (nu + n[g] > cap_n || pairs + cnt > kMaxUnionPairs)) break;
-            mem.push_back(Member{edge_offsets[g], pairs, cnt, (int32_t)nu, n[g]});
-            ids.push_back(g);
-            nu += n[g];
-            pairs += cnt;
-            i++;
-        }
+    for (const UnionPlan &up : plan) {
+        const int32_t hh = up.h;
+        const std::vector<Member> &mem = up.mem;
+        const std::vector<int32_t> &ids = up.ids;
+        const int64_t nu = up.n, pairs = up.pairs;
         if (pairs == 0) {  // no pairs at all: every member has zero edges
             for (size_t j = 0; j < mem.size(); j++) {
                 out_offsets[ids[j]] = out_pos;
@@ -260,5 +284,27 @@ extern "C" htd_status htd_truss_decompose_batched(
     }
     if (num_unions) *num_unions = unions;
     if (stats) *stats = acc;
+    return HTD_OK;
+}
+
+extern "C" htd_status htd_batch_plan(int32_t num_graphs, const int32_t *n, const int32_t *h,
+                                     const int64_t *edge_offsets, int32_t max_union_vertices,
+                                     int32_t *union_of, int32_t *vertex_offset, int32_t *num_unions) {
+    using namespace htd;
+    std::vector<UnionPlan> plan;
+    const htd_status ps = plan_unions("htd_batch_plan", num_graphs, n, h, edge_offsets,
+                                      max_union_vertices, &plan);
+    if (ps != HTD_OK) return ps;
+    if (num_graphs > 0 && (!union_of || !vertex_offset)) {
+        set_last_error("htd_batch_plan: NULL output array");
+        return HTD_EINVAL;
+    }
+    for (size_t u = 0; u < plan.size(); u++) {
+        for (size_t j = 0; j < plan[u].ids.size(); j++) {
+            union_of[plan[u].ids[j]] = (int32_t)u;
+            vertex_offset[plan[u].ids[j]] = plan[u].mem[j].voff;
+        }
+    }
+    if (num_unions) *num_unions = (int32_t)plan.size();
     return HTD_OK;
 }
