@@ -21,8 +21,9 @@
  *   - The caller owns every input and output buffer.  The library owns the graph handle
  *     and all scratch memory it allocates (stream-ordered, on the device of the call).
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is ordered after
- *     prior work on `stream`; every call below returns only after its results are
- *     complete and visible on `stream` (the calls synchronise internally).
+ *     prior work on `stream`; every call below except htd_h_support_static returns only
+ *     after its results are complete and visible on `stream` (the calls synchronise
+ *     internally).
  *   - On error nothing is written to the outputs; the handle stays valid unless stated.
  *   - Errors: HTD_EINVAL (bad argument: NULL pointer, h outside [1, HTD_MAX_H], n < 0,
  *     vertex id outside [0,n)), HTD_ENOMEM (device allocation failed), HTD_ECUDA (a CUDA
@@ -97,7 +98,9 @@ typedef struct htd_stats {
 } htd_stats;
 
 /* Option flags for htd_truss_decompose_ex. */
-#define HTD_OPT_TIMING 1u    /* time ball-build and h-support launches with CUDA events */
+#define HTD_OPT_TIMING 1u    /* time the initial ball-build and h-support launches and sample
+                                the round phases (CUDA events; the graph path times every
+                                16th batch of 16 rounds) into htd_stats */
 #define HTD_OPT_NO_GRAPH 2u  /* launch each peel round directly instead of via a CUDA graph */
 #define HTD_OPT_REBUILD 4u   /* h <= 2: rebuild shrunk balls and recompute their edges' support
                                 instead of the incremental lost-pair updates (same results) */
