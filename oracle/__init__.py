@@ -17,6 +17,9 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   the paper's surviving worked-example value (minimum 2-support 2 -> 2-trussness 4).
 * ``OracleGraph.certify`` -- pinned: accepts the oracle's own decompositions and rejects
   planted errors (t off by one, stamps swapped) on small graphs.
+* ``certify_all`` (``htd_cert.c``, multithreaded) -- pinned: its h-supports in the growing
+  subgraphs equal Floyd-Warshall's on every edge; it accepts every oracle decomposition
+  and rejects every claim with a wrong trussness (``tests/test_cert_pins.py``).
 """
 
 from __future__ import annotations
@@ -30,6 +33,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "htd_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "htd_cert.c")]
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle_htd.so")
 _lock = threading.Lock()
@@ -40,10 +44,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc into oracle/_build/liboracle_htd.so (portable flags)."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(s) for s in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC])
+    subprocess.check_call(["gcc", "-O3", "-std=gnu11", "-fPIC", "-shared", "-pthread", "-o", tmp,
+                           *_SRCS])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -75,6 +80,8 @@ def _load():
         lib.htdo_check_stamp_order.restype = i64
         lib.htdo_hindex.argtypes = [p, i32, i32, i32, p, p]
         lib.htdo_hindex.restype = i32
+        lib.htdo_certify_all.argtypes = [i32, i64, p, p, i32, p, p, i32, p, p, p, p]
+        lib.htdo_certify_all.restype = i64
         _lib = lib
         return lib
 
@@ -183,3 +190,40 @@ class OracleGraph:
         idx = np.nonzero(fails)[0]
         bad_edges = idx if ed is None else ed[idx]
         return order_bad, bad_edges, fails[idx]
+
+
+def certify_all(n: int, eu, ev, h: int, t, stamp, threads: int | None = None,
+                sups: bool = False):
+    """All-edge peeling certificate of a claimed decomposition (``htd_cert.c``).
+
+    Checks, on every edge, that stamps are ordered like t, validity (sup in {t >= t(e)}
+    at least t(e)-2) and removability (sup in {stamp >= stamp(e)} at most t(e)-2); the
+    three together prove t exact.  Returns (order_bad, failing_edges, fail_codes) and,
+    with ``sups``, also (sup_rem, sup_val).  fail code bit 1 = validity, bit 2 =
+    removability.  order_bad > 0 means nothing else was checked."""
+    lib = _load()
+    eu = np.ascontiguousarray(eu, dtype=np.int32)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    t = np.ascontiguousarray(t, dtype=np.int32)
+    stamp = np.ascontiguousarray(stamp, dtype=np.int32)
+    m = eu.size
+    if not (ev.size == t.size == stamp.size == m):
+        raise ValueError("edge, t and stamp arrays differ in length")
+    if threads is None:
+        threads = os.cpu_count() or 1
+    fail = np.zeros(max(1, m), dtype=np.int32)
+    sr = np.full(max(1, m), -1, dtype=np.int32) if sups else None
+    sv = np.full(max(1, m), -1, dtype=np.int32) if sups else None
+    ob = ctypes.c_int64(0)
+    rc = lib.htdo_certify_all(int(n), m, _ptr(eu), _ptr(ev), int(h), _ptr(t), _ptr(stamp),
+                              int(threads), _ptr(fail), _ptr(sr), _ptr(sv), ctypes.byref(ob))
+    if rc == -1:
+        raise MemoryError("certificate: allocation failed")
+    if rc == -2:
+        raise ValueError("certificate: bad argument (h out of range or a stamp outside [0, m])")
+    fail = fail[:m]
+    idx = np.nonzero(fail)[0]
+    out = (int(ob.value), idx, fail[idx])
+    if sups:
+        out = out + (sr[:m], sv[:m])
+    return out
