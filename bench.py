@@ -25,7 +25,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from synth import config_graph, rmat  # noqa: E402
+from synth import config_graph  # noqa: E402
 
 WORKLOADS = {
     "rmat_s18_h2": ("rmat_s18", 2),
@@ -34,6 +34,9 @@ WORKLOADS = {
     "er_n2000_h2": ("er_n2000", 2),
     "rmat_s16_h2": ("rmat_s16", 2),
 }
+# the other single-GPU workloads reported beside the headline (fewer steps each)
+CONFIG_ENTRIES = ["er_n2000_h2", "dcsbm_n200k_h2", "dcsbm_n200k_h3"]
+CONFIG_STEPS = {"dcsbm_n200k_h3": (1, 0)}  # (timed steps, warm-up steps); default (3, 1)
 METRIC = "edges decomposed/sec"
 UNIT = "edges/s"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
@@ -131,26 +134,38 @@ def job_throughput(units_per_replica: int, steps: int, t_max_ms: float, world: i
     return world * units_per_replica * steps / (t_max_ms / 1e3)
 
 
+def host_cpu():
+    """Host core count and CPU model (the CPU baseline runs on these cores)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
 def oracle_sample(budget_s: float, h: int):
-    """The CPU oracle, as it stands, on down-scaled R-MAT graphs with the workload's
-    generator parameters: scales grow until the cumulative time passes the budget.
-    Returns (edges/s of the largest completed scale, description, seconds)."""
+    """The CPU oracle, as it stands, on the 2,000-vertex Erdos-Renyi workload (G(2000,
+    8000), the workload the oracle finishes in seconds), one thread: the median of up to
+    three full decompositions within the budget.  Returns (edges/s, description, seconds
+    of one decomposition)."""
     import oracle
 
     oracle.build()
-    spent, best = 0.0, None
-    for scale in range(8, 16):
-        s, d = rmat(scale, 8, 0.57, 0.19, 0.19, 0x48545256)
-        og = oracle.OracleGraph.from_raw(1 << scale, s, d)
+    spec = config_graph("er_n2000")
+    og = oracle.OracleGraph.from_raw(spec.n, spec.src, spec.dst)
+    times = []
+    while len(times) < 3 and (not times or sum(times) + times[-1] < budget_s):
         t0 = time.perf_counter()
         og.truss_decompose(h)
-        dt = time.perf_counter() - t0
-        spent += dt
-        best = (og.m / dt, f"oracle full decomposition of R-MAT scale {scale} "
-                           f"(m={og.m}, same a,b,c,d, h={h}), single thread", dt)
-        if spent > budget_s or dt * 6 > budget_s:
-            break
-    return best
+        times.append(time.perf_counter() - t0)
+    dt = float(np.median(times))
+    return (og.m / dt, f"oracle full decomposition of er_n2000 (G(2000,8000), m={og.m}, "
+                       f"h={h}), single thread, median of {len(times)}", dt)
 
 
 def run_reference(args, world, rank):
@@ -177,6 +192,162 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def round_bytes_host(n: int, eu: np.ndarray, ev: np.ndarray, stamp: np.ndarray, h: int):
+    """Algorithmic bytes of the peel rounds, counted on the host from the graph and the round
+    log (each edge's removal round), independently of the kernels' own counters.
+
+    Per removed edge (a,b) of round s, with deg_s(x) the alive degree at the start of s:
+      * selection: 8 B (the edge's bucket entry and its alive mark);
+      * loss detection (h = 2): one candidate pair per old neighbour of either endpoint
+        ({a,b}, {a, N(b)}, {b, N(a)}: deg_s(a) + deg_s(b) - 1 pairs; h = 1: the pair {a,b}),
+        each 8 B: the adjacency slot that names it and one alive-adjacency word.
+    Returns a dict of byte totals and counts for the whole peel."""
+    m = eu.size
+    if m == 0:
+        return {"select": 0.0, "detect": 0.0, "pairs": 0, "frontier": 0}
+    st = stamp.astype(np.int64)
+    smax = int(st.max())
+    x = np.concatenate([eu, ev]).astype(np.int64)
+    s2 = np.concatenate([st, st])
+    # alive degree of x at the start of round s = x's edges with stamp >= s
+    key = x * (smax + 1) + (smax - s2)
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    xs = x[order]
+    block_start = np.searchsorted(xs, xs, side="left")
+    run_end = np.searchsorted(ks, ks, side="right")
+    deg_sorted = run_end - block_start
+    deg = np.empty(2 * m, dtype=np.int64)
+    deg[order] = deg_sorted
+    da, db = deg[:m], deg[m:]
+    pairs = (da + db - 1) if h >= 2 else np.ones(m, dtype=np.int64)
+    return {"select": 8.0 * m, "detect": 8.0 * float(pairs.sum()), "pairs": int(pairs.sum()),
+            "frontier": int(m)}
+
+
+def _phase_classes(st, h):
+    """Round kernels of a decomposition and their sampled device ms per timed slot."""
+    timed = max(1, st["timed_slots"])
+    if st["incremental"]:
+        return [("k_inc_select", st["ms_select"] / timed),
+                ("k_loss_detect", st["ms_find"] / timed),
+                ("k_loss_delta", st["ms_update"] / timed),
+                ("k_loss_apply_reduce", st["ms_minreduce"] / timed)]
+    return [("k_select", st["ms_select"] / timed),
+            ("k_cand_*", st["ms_find"] / timed),
+            ("k_remove", st["ms_remove"] / timed),
+            ("k_ball (rebuild)", st["ms_ball"] / timed),
+            ("k_make_items + k_hsup (rounds)", st["ms_update"] / timed),
+            ("k_minreduce", st["ms_minreduce"] / timed)]
+
+
+def measure_workload(htd, torch, lib, name, h, steps, warmup, flush, stream, dev, peaks,
+                     profile=True, e2e=False):
+    """Times `steps` steps (CSR build + decomposition, inputs in HBM, no timing flag) after
+    `warmup` untimed ones, then runs one untimed profiling step with the phase events and
+    stamps.  Returns the per-workload record (without the job-level keys)."""
+    spec = config_graph(name)
+    src_d = torch.from_numpy(spec.src).to(dev)
+    dst_d = torch.from_numpy(spec.dst).to(dev)
+
+    def step(flags, stamps=False):
+        g = htd.htd_build_csr(spec.n, src_d, dst_d)
+        t, stamp, st = htd.htd_truss_decompose(g, h, stamps=stamps, flags=flags)
+        m = g.m
+        eu, ev = htd.htd_edges(g) if stamps else (None, None)
+        g.free()
+        return m, st, (eu, ev, stamp)
+
+    for _ in range(warmup):
+        flush.zero_()
+        step(0)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    stats, m = [], 0
+    launches0 = lib.htd_kernel_launch_count()
+    for i in range(steps):
+        flush.zero_()  # untimed: evicts L2 between steps
+        ev[i][0].record(stream)
+        m, st, _ = step(0)
+        ev[i][1].record(stream)
+        stats.append(st)
+    torch.cuda.synchronize()
+    launches = (lib.htd_kernel_launch_count() - launches0) // max(1, steps)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = float(np.mean(ms))
+    s0 = stats[-1]
+    rec = {"workload": f"{name}_h{h}", "n": spec.n, "m": m, "h": h, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms_step, "edges_per_sec": m / (ms_step / 1e3),
+           "rounds": s0["rounds"], "levels": s0["levels"], "max_truss": s0["max_truss"],
+           "incremental": s0["incremental"], "gpu_launches": int(launches),
+           "kernel_counters": {"pairs_tested": s0["pairs_tested"], "pairs_lost": s0["pairs_lost"],
+                               "member_tests": s0["member_tests"],
+                               "edge_refreshes_per_endpoint": s0["hsup_evals"] - m,
+                               "alg_bytes_detect": s0["alg_bytes_detect"],
+                               "alg_bytes_update": s0["alg_bytes_update"],
+                               "alg_bytes_ball": s0["alg_bytes_ball"],
+                               "alg_bytes_hsup": s0["alg_bytes_hsup"]}}
+    if not profile:
+        return rec, ms, stats
+    # profiling step (untimed): CSR build time, initial pass, sampled phase times, stamps
+    flush.zero_()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    g = htd.htd_build_csr(spec.n, src_d, dst_d)
+    c1.record(stream)
+    t, stamp, stp = htd.htd_truss_decompose(g, h, stamps=True, flags=htd.HTD_OPT_TIMING)
+    eu, evv = htd.htd_edges(g)
+    g.free()
+    torch.cuda.synchronize()
+    ms_csr = c0.elapsed_time(c1)
+    ms_init = stp["ms_initial_ball"] + stp["ms_initial_hsup"]
+    # the untimed step's round time, split over the round kernels by their sampled shares
+    rounds_ms = max(0.0, ms_step - ms_csr - ms_init)
+    per_slot = _phase_classes(stp, h)
+    tot = sum(v for _, v in per_slot) or 1.0
+    slots = max(1, stp["slots"])
+    phases = {"csr_build": {"ms": ms_csr, "launches": None},
+              "k_ball (initial)": {"ms": stp["ms_initial_ball"], "launches": 1,
+                                   # count and store passes count the same bytes
+                                   "alg_bytes_kernel": (stp["alg_bytes_ball"] / 2
+                                                        if stp["incremental"] else None)},
+              "k_hsup (initial)": {"ms": stp["ms_initial_hsup"], "launches": 1,
+                                   "alg_bytes_kernel": stp["alg_bytes_hsup"]}}
+    for kname, v in per_slot:
+        phases[kname] = {"ms": rounds_ms * v / tot, "launches": slots, "share_of_rounds": v / tot}
+    hb = round_bytes_host(spec.n, host_np(eu), host_np(evv), host_np(stamp), h)
+    if stp["incremental"]:
+        phases["k_inc_select"]["alg_bytes_host"] = hb["select"]
+        phases["k_loss_detect"]["alg_bytes_host"] = hb["detect"]
+        phases["k_loss_detect"]["alg_bytes_kernel"] = stp["alg_bytes_detect"]
+        phases["k_loss_delta"]["alg_bytes_kernel"] = stp["alg_bytes_update"]
+    else:
+        phases["k_select"]["alg_bytes_host"] = hb["select"]
+    rec["phases_ms_per_step"] = phases
+    rec["phases_sum_over_step"] = sum(p["ms"] for p in phases.values()) / ms_step
+    rec["host_round_counts"] = {"frontier_edges": hb["frontier"], "candidate_pairs": hb["pairs"]}
+    # h-support evaluations: the initial pass computes every edge's h-support from scratch
+    rec["hsup_evals_per_sec_initial"] = m / (ms_init / 1e3) if ms_init > 0 else None
+    # dominant kernel and its roofline (host-counted bytes where defined)
+    kern = max((k for k in phases if k != "csr_build"), key=lambda k: phases[k]["ms"])
+    kp = phases[kern]
+    byts = kp.get("alg_bytes_host", kp.get("alg_bytes_kernel"))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = (byts / (kp["ms"] / 1e3)) / 1e9 if (byts and kp["ms"] > 0) else None
+    rec["roofline"] = {"kernel": kern, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                       "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
+                       "bytes_source": "host" if "alg_bytes_host" in kp else "kernel",
+                       "alg_bytes_per_launch": (byts / kp["launches"]) if byts else None,
+                       "launches_per_step": kp["launches"],
+                       "ms_per_launch": kp["ms"] / kp["launches"] if kp["launches"] else None}
+    return rec, ms, stats
+
+
+def host_np(t):
+    return t.cpu().numpy() if t is not None else None
+
+
 def run_gpu(args, world, rank, local):
     import torch
 
@@ -188,49 +359,25 @@ def run_gpu(args, world, rank, local):
         cuda_build.build()
     if world > 1:
         torch.distributed.barrier()
-    htd._lib.load()
     lib = htd._lib.load()
     name, h = WORKLOADS[args.workload]
-    spec = config_graph(name)
     dev = torch.device("cuda", local)
-    src_d = torch.from_numpy(spec.src).to(dev)
-    dst_d = torch.from_numpy(spec.dst).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
+    peaks, peak_kind = measured_peaks()
 
-    def step(flags):
-        g = htd.htd_build_csr(spec.n, src_d, dst_d)
-        t, _, st = htd.htd_truss_decompose(g, h, flags=flags)
-        m = g.m
-        g.free()
-        return m, st
-
-    for _ in range(args.warmup):
-        flush.zero_()
-        step(htd.HTD_OPT_TIMING)
-    torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    stats, m = [], 0
-    launches0 = lib.htd_kernel_launch_count()
     with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.zero_()  # untimed: evicts L2 between steps
-            ev[i][0].record(stream)
-            m, st = step(htd.HTD_OPT_TIMING)
-            ev[i][1].record(stream)
-            stats.append(st)
-        torch.cuda.synchronize()
-    launches = lib.htd_kernel_launch_count() - launches0
-    ms = [a.elapsed_time(b) for a, b in ev]
+        rec, ms, stats = measure_workload(htd, torch, lib, name, h, args.steps, args.warmup,
+                                          flush, stream, dev, peaks, profile=(rank == 0))
+    m = rec["m"]
     t_max = max_over_ranks(float(np.sum(ms)), world, dev)
     ms_step = t_max / args.steps
     value = job_throughput(m, args.steps, t_max, world)
 
     # end to end through the host-buffer entry point (pinned buffers, copies inside)
+    spec = config_graph(name)
     e2e_value, e2e_ms = None, []
     k = spec.src.size
     if not args.no_e2e:
@@ -250,82 +397,62 @@ def run_gpu(args, world, rank, local):
 
     if rank != 0:
         return
-    peaks, peak_kind = measured_peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    s0 = stats[-1]
-
-    def mean(key):
-        return float(np.mean([s[key] for s in stats]))
-
-    slots = max(1, s0["slots"])
-    timed = max(1, s0["timed_slots"])
-    m_edges = float(m)
-    # kernel classes of one step: (name, device ms per step, launches per step, alg bytes)
-    if s0["round_kernel_launches"] > 0:  # persistent round kernel
-        scan = 8.0 * m_edges * slots  # two passes over the supports per slot
-        classes = [("k_rounds_persistent", mean("ms_round_kernel"), s0["round_kernel_launches"],
-                     mean("alg_bytes_detect") + mean("alg_bytes_update") + scan)]
-    elif s0["incremental"]:
-        # phase times are sampled (every 16th batch); scale the per-slot mean to all slots
-        per = slots / timed
-        classes = [
-            ("k_loss_detect", mean("ms_find") * per, slots, mean("alg_bytes_detect")),
-            ("k_loss_delta", mean("ms_update") * per, slots, mean("alg_bytes_update")),
-            ("k_inc_select", mean("ms_select") * per, slots, 4.0 * m_edges * slots),
-            ("k_loss_apply_reduce", mean("ms_minreduce") * per, slots, 4.0 * m_edges * slots),
-        ]
-    else:
-        per = slots / timed
-        classes = [("k_ball (rebuild rounds)", mean("ms_ball") * per, slots, None),
-                   ("k_hsup (rounds)", mean("ms_update") * per, slots, None)]
-    classes += [
-        ("k_ball (initial store)", mean("ms_initial_ball"), 1, mean("alg_bytes_ball") / 2),
-        ("k_hsup (initial)", mean("ms_initial_hsup"), 1, mean("alg_bytes_hsup")),
-    ]
-    kern, k_ms, k_launches, k_bytes = max(classes, key=lambda c: c[1])
-    achieved = (k_bytes / (k_ms / 1e3)) / 1e9 if (k_bytes and k_ms > 0) else None
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                tj = json.load(f)
-            ent = tj.get(args.workload, {}).get(kern)
-            if ent:
-                traffic = ent.get("bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
-    phases = {name: {"ms": ms, "launches": ln, "alg_bytes": b} for name, ms, ln, b in classes}
-    hsup_rate = float(np.mean([s["hsup_evals"] for s in stats])) / (ms_step / 1e3)
+    # the other single-GPU workloads, fewer steps each (their own records)
+    configs = {}
+    for wl in ([] if args.no_configs else [w for w in CONFIG_ENTRIES if w != args.workload]):
+        cname, ch = WORKLOADS[wl]
+        st_, wu_ = CONFIG_STEPS.get(wl, (3, 1))
+        rc, _, _ = measure_workload(htd, torch, lib, cname, ch, st_, wu_, flush, stream, dev,
+                                    peaks, profile=True)
+        configs[wl] = rc
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         v, desc, dt = oracle_sample(args.cpu_budget, h)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds_per_decomposition": dt, "host": host_cpu(),
+               "workloads": {"er_n2000_h2": {"value": v, "unit": UNIT, "seconds": dt},
+                             "rmat_s18_h2": "did not finish in budget (naive oracle; the "
+                                            "initial pass alone is ~1e11 BFS steps)",
+                             "dcsbm_n200k_h2": "did not finish in budget",
+                             "dcsbm_n200k_h3": "did not finish in budget"}}
+        if "er_n2000_h2" in configs:
+            configs["er_n2000_h2"]["oracle_seconds"] = dt
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "graph": spec.recipe, "n": spec.n, "m": m, "h": h,
                    "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
-                   "l2": "256 MiB buffer written between timed steps (untimed)"},
-        "hsup_evals_per_sec": hsup_rate,
-        "rounds": s0["rounds"], "levels": s0["levels"], "max_truss": s0["max_truss"],
-        "hsup_evals": s0["hsup_evals"], "pairs_tested": s0["pairs_tested"],
-        "pairs_lost": s0["pairs_lost"], "member_tests": s0["member_tests"],
-        "phases_ms_per_step": phases,
-        "roofline": {"kernel": kern, "bound": "hbm", "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
-                     "traffic": traffic, "peak_source": peak_kind,
-                     "alg_bytes_per_launch": (k_bytes / k_launches) if k_bytes else None,
-                     "launches_per_step": k_launches, "ms_per_launch": k_ms / k_launches},
+                   "l2": "256 MiB buffer written between timed steps (untimed)",
+                   "timed_flags": "none (phase times come from one extra untimed step)"},
+        "rounds": rec["rounds"], "levels": rec["levels"], "max_truss": rec["max_truss"],
+        "hsup_evals_per_sec_initial": rec.get("hsup_evals_per_sec_initial"),
+        "phases_ms_per_step": rec.get("phases_ms_per_step"),
+        "phases_sum_over_step": rec.get("phases_sum_over_step"),
+        "host_round_counts": rec.get("host_round_counts"),
+        "kernel_counters": rec["kernel_counters"],
+        "roofline": dict(rec.get("roofline", {}), peak_source=peak_kind,
+                         traffic=profile_traffic(args.workload, rec.get("roofline", {}).get("kernel"))),
         "e2e": None if e2e_value is None else {
             "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(8 * k),
             "d2h_bytes_per_step": int(12 * m), "ms_per_step": float(np.mean(e2e_ms))},
-        "gpu_launches": int(launches // args.steps),
+        "gpu_launches": rec["gpu_launches"],
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
+        "configs": configs,
     }
     print(json.dumps(line), flush=True)
+
+
+def profile_traffic(workload, kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if any."""
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(prof) as f:
+            ent = json.load(f).get(workload, {}).get(kernel)
+        return ent.get("bytes_per_launch") if ent else None
+    except (OSError, ValueError, AttributeError):
+        return None
 
 
 def main():
@@ -338,6 +465,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other single-GPU workloads' entries")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if world > 1:

@@ -230,11 +230,14 @@ htd_status htd_batch_plan(int32_t num_graphs, const int32_t *n, const int32_t *h
  * Unlike the other calls this one only enqueues work on `stream` (NULL = legacy default
  * stream) and returns; the result is ready when the stream reaches that point.  The first
  * call on a device looks up the scratch array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Every call shares the one scratch
+ * make that first call before any stream capture.  The address is kept for the life of
+ * the process: after cudaDeviceReset (which invalidates every device address) do not call
+ * this entry point again in the same process.  Every call shares the one scratch
  * array and reuses what the previous call left there: calls that overlap on the GPU (two
  * streams, or two threads) race and must be serialised by the caller.  Errors: EINVAL for
  * a NULL pointer or h outside [1, HTD_MAX_H], EUNSUPPORTED for n > HTD_STATIC_MAX_N or, at
- * h >= 3, when one block's level lists (2n int32) exceed the scratch, ECUDA otherwise. */
+ * h >= 3, when one block's level lists (2n int32) exceed the scratch, or when the
+ * device's per-block shared memory cannot hold two n-bit sets; ECUDA otherwise. */
 #define HTD_STATIC_MAX_N 786432
 htd_status htd_h_support_static(int32_t n, const int32_t *row_ptr_dev, const int32_t *col_dev,
                                 int64_t m, const int32_t *eu_dev, const int32_t *ev_dev,

@@ -171,7 +171,15 @@ extern "C" htd_status htd_h_support_static(int32_t n, const int32_t *row_ptr_dev
     }
     const int W = (n + 31) / 32 > 0 ? (n + 31) / 32 : 1;
     const size_t smem = (size_t)2 * W * sizeof(uint32_t);
-    int occ = 0;
+    int occ = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_hsup_static);
+    if (e == cudaSuccess && smem + fa.sharedSizeBytes > (size_t)optin) {
+        // n is within HTD_STATIC_MAX_N but this device's blocks cannot hold two n-bit sets
+        set_last_error("htd_h_support_static: two n-bit sets do not fit in this device's shared memory");
+        return HTD_EUNSUPPORTED;
+    }
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_hsup_static, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)

@@ -52,15 +52,26 @@ def static_h_support(htd, g, h):
     return out
 
 
-def test_static_entry_point_matches_h_support_on_consecutive_calls(htd):
+def test_static_entry_point_matches_h_support_on_consecutive_calls(htd, oracle_mod):
+    # h = 1 (adjacency only), h = 2, and h = 3..5 (the level lists swap from depth 4 on);
+    # the R-MAT graphs have hubs, so the deep levels are large.  Each result is compared
+    # with htd_h_support and with the oracle's per-edge BFS.
     cases = [(1 << 9, rmat(9, 8, 0.57, 0.19, 0.19, 501), 2),
              (400, erdos_renyi_gnm(400, 1600, 502), 3),
-             (1 << 9, rmat(9, 8, 0.57, 0.19, 0.19, 501), 2)]
+             (1 << 9, rmat(9, 8, 0.57, 0.19, 0.19, 501), 2),
+             (1 << 10, rmat(10, 8, 0.57, 0.19, 0.19, 503), 1),
+             (600, erdos_renyi_gnm(600, 1500, 504), 4),
+             (1 << 10, rmat(10, 4, 0.57, 0.19, 0.19, 505), 5),
+             (1 << 10, rmat(10, 4, 0.57, 0.19, 0.19, 505), 4)]
     for n, (s, d), h in cases:
         g = htd.htd_build_csr(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
         ref = htd.htd_h_support(g, h)
         got = static_h_support(htd, g, h)
+        again = static_h_support(htd, g, h)  # back to back on the shared scratch
         assert torch.equal(got, ref), (n, h)
+        assert torch.equal(again, ref), (n, h)
+        og = oracle_mod.OracleGraph.from_raw(n, s, d)
+        np.testing.assert_array_equal(got.cpu().numpy(), og.h_support(h), err_msg=f"n={n} h={h}")
         g.free()
 
 
