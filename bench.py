@@ -37,6 +37,10 @@ WORKLOADS = {
 # the other single-GPU workloads reported beside the headline (fewer steps each)
 CONFIG_ENTRIES = ["er_n2000_h2", "dcsbm_n200k_h2", "dcsbm_n200k_h3"]
 CONFIG_STEPS = {"dcsbm_n200k_h3": (1, 0)}  # (timed steps, warm-up steps); default (3, 1)
+# served stream: Poisson arrivals at 200 requests/s over R-MAT and BA graphs, h in {2, 3}
+# (the largest pool members are capped so that the stream finishes within the bench run)
+SERVED = {"count": 200, "seed": 0x48545259, "rate": 200.0, "workers": 4,
+          "rmat_scales": (10, 15), "ba_n": (1_000, 50_000)}
 METRIC = "edges decomposed/sec"
 UNIT = "edges/s"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
@@ -228,6 +232,12 @@ def round_bytes_host(n: int, eu: np.ndarray, ev: np.ndarray, stamp: np.ndarray, 
 def _phase_classes(st, h):
     """Round kernels of a decomposition and their sampled device ms per timed slot."""
     timed = max(1, st["timed_slots"])
+    if st["incremental"] and h == 3:
+        return [("k_inc_select", st["ms_select"] / timed),
+                ("k_loss_detect (radius 2, radius-3 items)", st["ms_remove"] / timed),
+                ("k_loss3_test", st["ms_find"] / timed),
+                ("k_loss_delta", st["ms_update"] / timed),
+                ("k_loss_apply_reduce", st["ms_minreduce"] / timed)]
     if st["incremental"]:
         return [("k_inc_select", st["ms_select"] / timed),
                 ("k_loss_detect", st["ms_find"] / timed),
@@ -282,6 +292,9 @@ def measure_workload(htd, torch, lib, name, h, steps, warmup, flush, stream, dev
            "rounds": s0["rounds"], "levels": s0["levels"], "max_truss": s0["max_truss"],
            "incremental": s0["incremental"], "gpu_launches": int(launches),
            "kernel_counters": {"pairs_tested": s0["pairs_tested"], "pairs_lost": s0["pairs_lost"],
+                               "pairs3_tested": s0["pairs3_tested"],
+                               "pairs2_lost": s0["pairs2_lost"],
+                               "rounds_rebuilt": s0["rounds_rebuilt"],
                                "member_tests": s0["member_tests"],
                                "edge_refreshes_per_endpoint": s0["hsup_evals"] - m,
                                "alg_bytes_detect": s0["alg_bytes_detect"],
@@ -317,7 +330,12 @@ def measure_workload(htd, torch, lib, name, h, steps, warmup, flush, stream, dev
     for kname, v in per_slot:
         phases[kname] = {"ms": rounds_ms * v / tot, "launches": slots, "share_of_rounds": v / tot}
     hb = round_bytes_host(spec.n, host_np(eu), host_np(evv), host_np(stamp), h)
-    if stp["incremental"]:
+    if stp["incremental"] and h == 3:
+        phases["k_inc_select"]["alg_bytes_host"] = hb["select"]
+        phases["k_loss_detect (radius 2, radius-3 items)"]["alg_bytes_host"] = hb["detect"]
+        phases["k_loss3_test"]["alg_bytes_kernel"] = stp["alg_bytes_detect"]
+        phases["k_loss_delta"]["alg_bytes_kernel"] = stp["alg_bytes_update"]
+    elif stp["incremental"]:
         phases["k_inc_select"]["alg_bytes_host"] = hb["select"]
         phases["k_loss_detect"]["alg_bytes_host"] = hb["detect"]
         phases["k_loss_detect"]["alg_bytes_kernel"] = stp["alg_bytes_detect"]
@@ -342,6 +360,44 @@ def measure_workload(htd, torch, lib, name, h, steps, warmup, flush, stream, dev
                        "launches_per_step": kp["launches"],
                        "ms_per_launch": kp["ms"] / kp["launches"] if kp["launches"] else None}
     return rec, ms, stats
+
+
+def measure_served(htd, count: int, seed: int, rate: float, workers: int, rmat_scales, ba_n):
+    """Served form: a Poisson request stream submitted on its arrival schedule to a server
+    (continuous batching, admission by device memory); throughput and latency percentiles
+    over the whole stream.  Graph generation happens before the stream starts."""
+    from synth import served_requests
+
+    reqs = served_requests(count, seed, rate, rmat_scales, ba_n)
+    srv = htd.Server(workers=workers)
+    try:
+        ids = []
+        t0 = time.perf_counter()
+        for arr, n, s, d, h, _ in reqs:
+            now = time.perf_counter() - t0
+            if arr > now:
+                time.sleep(arr - now)
+            ids.append(srv.submit(n, s, d, h))
+        infos = [srv.wait(rid, r[2].size)[3] for rid, r in zip(ids, reqs)]
+        sinfo = srv.info()
+    finally:
+        srv.close()
+    lat = np.array([i["done_s"] - i["submit_s"] for i in infos]) * 1e3
+    wait = np.array([i["start_s"] - i["submit_s"] for i in infos]) * 1e3
+    span = max(i["done_s"] for i in infos) - min(i["submit_s"] for i in infos)
+    edges = float(sum(i["m"] for i in infos))
+    return {"workload": "served_poisson", "requests": count, "offered_rate_per_s": rate,
+            "pool": {"rmat_scales": list(rmat_scales), "ba_n": list(ba_n), "h": [2, 3],
+                     "seed": seed},
+            "workers": workers, "edges": edges, "span_s": span,
+            "edges_per_sec": edges / span, "requests_per_sec": count / span,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "queue_wait_ms": {"p50": float(np.percentile(wait, 50)),
+                              "p99": float(np.percentile(wait, 99))},
+            "peak_running": sinfo["peak_running"], "budget_bytes": sinfo["budget_bytes"],
+            "peak_reserved_bytes": sinfo["peak_reserved_bytes"],
+            "retries": int(sum(i["retries"] for i in infos))}
 
 
 def host_np(t):
@@ -405,6 +461,10 @@ def run_gpu(args, world, rank, local):
         rc, _, _ = measure_workload(htd, torch, lib, cname, ch, st_, wu_, flush, stream, dev,
                                     peaks, profile=True)
         configs[wl] = rc
+    if not args.no_served:
+        configs["served_poisson"] = measure_served(htd, SERVED["count"], SERVED["seed"],
+                                                   SERVED["rate"], SERVED["workers"],
+                                                   SERVED["rmat_scales"], SERVED["ba_n"])
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         v, desc, dt = oracle_sample(args.cpu_budget, h)
@@ -467,6 +527,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other single-GPU workloads' entries")
+    ap.add_argument("--no-served", action="store_true", help="skip the served-stream entry")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if world > 1:

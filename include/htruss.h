@@ -95,6 +95,10 @@ typedef struct htd_stats {
     int32_t incremental;     /* 1 if the rounds used incremental support updates */
     int32_t reserved;
     int64_t slots;           /* round slots that ran (rounds plus continued batches) */
+    int64_t pairs3_tested;   /* incremental h = 3 rounds: radius-3 candidate pairs tested */
+    int64_t pairs2_lost;     /* incremental h = 3 rounds: pairs that left radius-2 balls */
+    int64_t rounds_rebuilt;  /* incremental h = 3 rounds that ran out of room and were
+                                finished by rebuilding the candidates' balls */
 } htd_stats;
 
 /* Option flags for htd_truss_decompose_ex. */
@@ -102,19 +106,24 @@ typedef struct htd_stats {
                                 the round phases (CUDA events; the graph path times every
                                 16th batch of 16 rounds) into htd_stats */
 #define HTD_OPT_NO_GRAPH 2u  /* launch each peel round directly instead of via a CUDA graph */
-#define HTD_OPT_REBUILD 4u   /* h <= 2: rebuild shrunk balls and recompute their edges' support
+#define HTD_OPT_REBUILD 4u   /* h <= 3: rebuild shrunk balls and recompute their edges' support
                                 instead of the incremental lost-pair updates (same results) */
 #define HTD_OPT_PERSISTENT_ROUNDS 16u  /* h <= 2: all rounds in a persistent cooperative
                                           kernel (phases split by grid barriers) instead of
                                           a CUDA graph of 16 rounds (same results) */
-#define HTD_OPT_TINY_LOSS_TABLE 8u  /* h <= 2: 128-slot lost-pair table, so that rounds run in
-                                       many batches (a test of that path; slow) */
+#define HTD_OPT_TINY_LOSS_TABLE 8u  /* h <= 3: 128-slot lost-pair tables, so that h <= 2 rounds
+                                       run in many batches and h = 3 rounds are finished by
+                                       rebuilds (a test of those paths; slow) */
 #define HTD_OPT_COMPACT_BALLS 32u   /* h <= 2: store each ball in its smaller form (sorted
                                        non-zero words when at most half the words are
                                        non-zero) even when every ball fits dense; by default
                                        the incremental peel keeps all balls dense (one load
                                        per membership test) when the n x n bits fit in a
-                                       quarter of the free device memory (same results) */
+                                       quarter of the free device memory (same results).
+                                       h = 3: the incremental rounds need dense radius-2 and
+                                       radius-3 balls (two n x n bit sets in a third of the
+                                       free memory); with this flag, or when they do not
+                                       fit, h = 3 peels by rebuilds */
 
 /* Normalise an undirected edge list and build the graph (Sec. 2 graph model).
  *   n            vertex count, ids in [0, n); 0 <= n <= HTD_MAX_N.
@@ -242,6 +251,86 @@ htd_status htd_batch_plan(int32_t num_graphs, const int32_t *n, const int32_t *h
 htd_status htd_h_support_static(int32_t n, const int32_t *row_ptr_dev, const int32_t *col_dev,
                                 int64_t m, const int32_t *eu_dev, const int32_t *ev_dev,
                                 int32_t h, int32_t *sup_dev, void *stream);
+
+/* ---- Served decomposition: a request loop with continuous batching -------------------
+ *
+ * The paper decomposes one graph per call; a server decomposes a stream of independent
+ * requests, each an ordinary decomposition of its own graph (Def. 4; Sec. 3 peeling), so a
+ * result does not depend on the other requests.  Requests are admitted in arrival order
+ * while an estimate of their device footprint (htd_footprint_estimate) fits the server's
+ * memory budget beside the requests already admitted; a pool of worker threads, each with
+ * its own stream, runs the admitted requests concurrently (their rounds overlap on the
+ * device), keeps each request's graph and peel state on the device until its result is
+ * copied back, and releases its share of the budget when it finishes, admitting the next
+ * requests.  A request larger than the whole budget is admitted alone.  A request that runs
+ * out of device memory beside others is put back at the head of the queue and retried
+ * after they finish.  All calls are thread-safe. */
+typedef struct htd_server htd_server;
+
+/* Timing and outcome of one request (seconds since the server was created). */
+typedef struct htd_request_info {
+    int64_t m;               /* distinct edges of the request's graph */
+    int64_t est_bytes;       /* footprint estimate used for admission */
+    int64_t rounds;          /* peel rounds */
+    double submit_s;         /* htd_server_submit returned */
+    double admit_s;          /* admitted (fits the budget) */
+    double start_s;          /* a worker started it */
+    double done_s;           /* result on the host */
+    int32_t h;
+    int32_t status;          /* htd_status of the decomposition */
+    int32_t worker;          /* worker thread that ran it */
+    int32_t retries;         /* times it was put back after running out of memory */
+} htd_request_info;
+
+/* Server state for monitoring. */
+typedef struct htd_server_stats {
+    int64_t budget_bytes;
+    int64_t reserved_bytes;       /* estimates of the admitted and running requests */
+    int64_t peak_reserved_bytes;
+    int32_t workers;
+    int32_t running;              /* requests a worker is running now */
+    int32_t peak_running;         /* most requests run at the same time */
+    int32_t pending;              /* arrived, waiting for room in the budget */
+    int32_t admitted;             /* admitted, waiting for a worker */
+    int32_t pad;
+} htd_server_stats;
+
+/* Upper estimate of the device bytes one decomposition of a graph with n vertices and m_in
+ * raw pairs at hop threshold h takes (graph, peel state, balls; dense balls when they fit a
+ * quarter of free_bytes, as the decomposition itself chooses).  Host only.  Returns -1 for
+ * a negative n or m_in. */
+int64_t htd_footprint_estimate(int32_t n, int64_t m_in, int32_t h, int64_t free_bytes);
+
+/* Starts a server on the current device with `workers` threads (1..64).  budget_bytes: the
+ * device memory the admitted requests may take together (0: 80% of the memory free now).
+ * flags: HTD_OPT_* passed to every decomposition.  Errors: EINVAL, ECUDA. */
+htd_status htd_server_create(int32_t workers, int64_t budget_bytes, uint32_t flags,
+                             htd_server **out);
+
+/* Queues a decomposition of the graph given by m_in raw pairs (host arrays, copied before
+ * the call returns; normalised as htd_build_csr does) at hop threshold h.  *id_out receives
+ * the request id.  Errors: EINVAL (bad n, h, NULL pointer), EOVERFLOW (2*m_in >= 2^31);
+ * errors of the decomposition itself (a vertex id outside [0,n), ...) are returned by
+ * htd_server_wait. */
+htd_status htd_server_submit(htd_server *s, int32_t n, const int32_t *src_host,
+                             const int32_t *dst_host, int64_t m_in, int32_t h, int64_t *id_out);
+
+/* *done = 1 once the request's result is ready.  EINVAL for an unknown or collected id. */
+htd_status htd_server_poll(htd_server *s, int64_t id, int32_t *done);
+
+/* Waits for the request and collects it: canonical edges and t(e,h) into host buffers of
+ * `capacity` entries each (eu_host[e] < ev_host[e], lexicographic, as htd_edges), and its
+ * info (nullable).  Returns the decomposition's status; EINVAL (the request stays
+ * collectable, info->m set) if capacity < m.  A collected id is forgotten. */
+htd_status htd_server_wait(htd_server *s, int64_t id, int32_t *eu_host, int32_t *ev_host,
+                           int32_t *truss_host, int64_t capacity, htd_request_info *info);
+
+/* Budget, reservations and queue lengths now. */
+htd_status htd_server_info(htd_server *s, htd_server_stats *out);
+
+/* Lets the admitted requests finish, drops the ones still waiting for admission, stops the
+ * workers and frees the server (uncollected results are lost).  NULL is ignored. */
+void htd_server_destroy(htd_server *s);
 
 /* Frees the handle and every device buffer it owns (NULL is ignored). */
 void htd_graph_free(htd_graph *g);

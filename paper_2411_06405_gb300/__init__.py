@@ -28,7 +28,7 @@ __all__ = [
     "HtdStats",
     "Graph", "htd_build_csr", "htd_graph_info", "htd_edges", "htd_csr", "htd_h_support",
     "htd_truss_decompose", "htd_truss_decompose_host", "htd_h_support_static", "htd_graph_free",
-    "htd_truss_decompose_batched",
+    "htd_truss_decompose_batched", "Server", "htd_footprint_estimate",
     "library_path",
 ]
 
@@ -237,6 +237,70 @@ def htd_h_support_static(n: int, row_ptr, col, eu, ev, h: int, out, stream=None)
                                                 _ptr(eu), _ptr(ev), int(h), _ptr(out),
                                                 _stream_handle(stream)), "htd_h_support_static")
     return out
+
+
+class Server:
+    """A served-decomposition loop (htd_server_*): requests are admitted by device memory as
+    they arrive and run concurrently by worker threads; results come back on the host."""
+
+    def __init__(self, workers: int = 4, budget_bytes: int = 0, flags: int = 0):
+        h = ctypes.c_void_p()
+        _lib.check(_lib.load().htd_server_create(int(workers), int(budget_bytes), int(flags),
+                                                 ctypes.byref(h)), "htd_server_create")
+        self._h = h
+
+    def submit(self, n: int, src, dst, h: int) -> int:
+        """Queues a decomposition of the raw pairs (numpy int32 arrays, copied); returns
+        the request id."""
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        if src.shape != dst.shape:
+            raise ValueError("src and dst differ in length")
+        rid = ctypes.c_int64()
+        vp = lambda a: ctypes.c_void_p(a.ctypes.data) if a.size else None
+        _lib.check(_lib.load().htd_server_submit(self._h, int(n), vp(src), vp(dst), src.size,
+                                                 int(h), ctypes.byref(rid)), "htd_server_submit")
+        return int(rid.value)
+
+    def poll(self, rid: int) -> bool:
+        done = ctypes.c_int32()
+        _lib.check(_lib.load().htd_server_poll(self._h, int(rid), ctypes.byref(done)),
+                   "htd_server_poll")
+        return bool(done.value)
+
+    def wait(self, rid: int, capacity: int):
+        """Blocks until the request is done; returns (eu, ev, truss, info) as numpy arrays
+        trimmed to the request's m edges (capacity >= m, e.g. its number of raw pairs)."""
+        cap = max(1, int(capacity))
+        eu = np.empty(cap, np.int32)
+        ev = np.empty(cap, np.int32)
+        t = np.empty(cap, np.int32)
+        info = _lib.HtdRequestInfo()
+        vp = lambda a: ctypes.c_void_p(a.ctypes.data)
+        _lib.check(_lib.load().htd_server_wait(self._h, int(rid), vp(eu), vp(ev), vp(t), cap,
+                                               ctypes.byref(info)), "htd_server_wait")
+        m = int(info.m)
+        return eu[:m], ev[:m], t[:m], info.as_dict()
+
+    def info(self):
+        st = _lib.HtdServerStats()
+        _lib.check(_lib.load().htd_server_info(self._h, ctypes.byref(st)), "htd_server_info")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.load().htd_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def htd_footprint_estimate(n: int, m_in: int, h: int, free_bytes: int) -> int:
+    return int(_lib.load().htd_footprint_estimate(int(n), int(m_in), int(h), int(free_bytes)))
 
 
 def htd_graph_free(g: Graph):

@@ -32,6 +32,8 @@ EXPORTED = (
     "htd_truss_decompose", "htd_truss_decompose_ex", "htd_truss_decompose_host",
     "htd_graph_free", "htd_kernel_launch_count", "htd_status_string", "htd_last_error",
     "htd_h_support_static", "htd_truss_decompose_batched", "htd_batch_plan",
+    "htd_footprint_estimate", "htd_server_create", "htd_server_submit", "htd_server_poll",
+    "htd_server_wait", "htd_server_info", "htd_server_destroy",
 )
 
 
@@ -68,10 +70,49 @@ class HtdStats(ctypes.Structure):
         ("incremental", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
         ("slots", ctypes.c_int64),
+        ("pairs3_tested", ctypes.c_int64),
+        ("pairs2_lost", ctypes.c_int64),
+        ("rounds_rebuilt", ctypes.c_int64),
     ]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class HtdRequestInfo(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int64),
+        ("est_bytes", ctypes.c_int64),
+        ("rounds", ctypes.c_int64),
+        ("submit_s", ctypes.c_double),
+        ("admit_s", ctypes.c_double),
+        ("start_s", ctypes.c_double),
+        ("done_s", ctypes.c_double),
+        ("h", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("worker", ctypes.c_int32),
+        ("retries", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class HtdServerStats(ctypes.Structure):
+    _fields_ = [
+        ("budget_bytes", ctypes.c_int64),
+        ("reserved_bytes", ctypes.c_int64),
+        ("peak_reserved_bytes", ctypes.c_int64),
+        ("workers", ctypes.c_int32),
+        ("running", ctypes.c_int32),
+        ("peak_running", ctypes.c_int32),
+        ("pending", ctypes.c_int32),
+        ("admitted", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
 
 
 class HtdError(RuntimeError):
@@ -114,6 +155,14 @@ def load():
             "htd_truss_decompose_batched": ([i32, p, p, p, p, p, u32, i32, p, p, p,
                                              ctypes.POINTER(i32), ps, p], ctypes.c_int),
             "htd_batch_plan": ([i32, p, p, p, i32, p, p, ctypes.POINTER(i32)], ctypes.c_int),
+            "htd_footprint_estimate": ([i32, i64, i32, i64], i64),
+            "htd_server_create": ([i32, i64, u32, pp], ctypes.c_int),
+            "htd_server_submit": ([p, i32, p, p, i64, i32, ctypes.POINTER(i64)], ctypes.c_int),
+            "htd_server_poll": ([p, i64, ctypes.POINTER(i32)], ctypes.c_int),
+            "htd_server_wait": ([p, i64, p, p, p, i64, ctypes.POINTER(HtdRequestInfo)],
+                                ctypes.c_int),
+            "htd_server_info": ([p, ctypes.POINTER(HtdServerStats)], ctypes.c_int),
+            "htd_server_destroy": ([p], None),
             "htd_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "htd_last_error": ([], ctypes.c_char_p),
         }

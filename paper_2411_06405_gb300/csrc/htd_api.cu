@@ -247,8 +247,9 @@ htd_status htd_h_support(htd_graph *g, int32_t h, int32_t *sup_dev, void *stream
     Handle *H = &g->H;
     cudaStream_t user = static_cast<cudaStream_t>(stream);
     API_TRY(begin_call(H, user));
-    API_TRY(prepare_work(H, h, true));
+    API_TRY(prepare_work(H, h, h <= 2));
     H->w.dense_balls = false;  // h-support alone streams the smaller form of each ball
+    H->w.inc3 = false;
     int64_t launches = 0;
     htd_status ip = htd::initial_pass(H, h, H->pstream, &launches, nullptr);
     htd::g_launches += launches;
@@ -286,19 +287,25 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
 
     API_TRY(begin_call(H, user));
     bool incremental = (flags & HTD_OPT_REBUILD) == 0;
-    API_TRY(prepare_work(H, h, incremental, (flags & HTD_OPT_TINY_LOSS_TABLE) != 0));
-    incremental = w.incremental;
-    // the incremental peel's membership tests take one load on a dense ball, a binary search
-    // on a compact one: keep every ball dense when the n x n bits fit comfortably
-    w.dense_balls = false;
-    if (incremental && (flags & HTD_OPT_COMPACT_BALLS) == 0) {
+    {
+        // the incremental peel's membership tests take one load on a dense ball, a binary
+        // search on a compact one: keep every ball dense when the n x n bits fit comfortably.
+        // At h = 3 the incremental rounds need two dense ball sets (radius 2 and 3).
         size_t free_b = 0, total_b = 0;
         API_CHECK(cudaMemGetInfo(&free_b, &total_b));
-        const double dense_bytes = 4.0 * (double)H->g.n * (double)w.Wpad;
-        w.dense_balls = dense_bytes <= (double)free_b / 4 && dense_bytes < 4.0 * (double)((int64_t)1 << 33);
+        const double Wp = (double)(((H->g.n + 31) / 32 + 3) & ~3);
+        const double dense_bytes = 4.0 * (double)H->g.n * (Wp > 0 ? Wp : 4.0);
+        const bool fits = dense_bytes <= (double)free_b / 4 && dense_bytes < 4.0 * (double)((int64_t)1 << 33);
+        if (h == 3 && ((flags & HTD_OPT_COMPACT_BALLS) != 0 || !(2.0 * dense_bytes <= (double)free_b / 3) ||
+                       dense_bytes >= 4.0 * (double)((int64_t)1 << 33)))
+            incremental = false;
+        API_TRY(prepare_work(H, h, incremental, (flags & HTD_OPT_TINY_LOSS_TABLE) != 0));
+        incremental = w.incremental;
+        w.dense_balls = incremental && (h == 3 || ((flags & HTD_OPT_COMPACT_BALLS) == 0 && fits));
     }
     {
         htd_status ip = htd::initial_pass(H, h, H->pstream, &launches, timing ? &local : nullptr);
+        if (ip == HTD_OK) ip = htd::initial_pass_r2(H, H->pstream, &launches);
         htd::g_launches += launches;
         launches_counted = launches;
         API_TRY(ip);
@@ -308,8 +315,8 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
     API_CHECK(cudaStreamSynchronize(H->pstream));
     API_TRY(check_status_err(w.status_host));
 
-    const int per_round = incremental ? 4 : h + 6;
-    const bool persistent = incremental && (flags & HTD_OPT_PERSISTENT_ROUNDS) != 0;
+    const int per_round = w.inc3 ? 5 : incremental ? 4 : h + 6;
+    const bool persistent = incremental && h <= 2 && (flags & HTD_OPT_PERSISTENT_ROUNDS) != 0;
     if (persistent && w.status_host->alive > 0) {
         // one cooperative launch runs up to kPersistentSlots round slots; the host checks the
         // status block between launches
@@ -436,7 +443,18 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
                                       cudaMemcpyDeviceToHost, H->pstream));
             API_CHECK(cudaStreamSynchronize(H->pstream));
             API_TRY(check_status_err(w.status_host));
-            if (timed) {
+            const bool halted = w.status_host->halt != 0;
+            if (halted) {
+                // an h = 3 round ran out of room: finish it by rebuilds, then go on (the
+                // batch's sampled events then cover idle rounds and are not used)
+                API_TRY(htd::recover_round_h3(H, H->pstream, &launches));
+                count_launches();
+                API_CHECK(cudaMemcpyAsync(w.status_host, w.status, sizeof(htd::DevStatus),
+                                          cudaMemcpyDeviceToHost, H->pstream));
+                API_CHECK(cudaStreamSynchronize(H->pstream));
+                API_TRY(check_status_err(w.status_host));
+            }
+            if (timed && !halted) {
                 // only the slots that ran a round (or a batch of one) count; those after the
                 // last round are no-ops
                 const int64_t active = std::min<int64_t>(R, w.status_host->st_slots - slots_before);
@@ -501,7 +519,10 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
         local.alg_bytes_detect = (double)s->st_bytes_detect;
         local.alg_bytes_update = (double)s->st_bytes_update;
         local.kernel_launches = launches;
-        local.ball_pool_bytes = w.pool_used * 4;
+        local.ball_pool_bytes = (w.pool_used + (w.inc3 ? (int64_t)H->g.n * w.Wpad : 0)) * 4;
+        local.pairs3_tested = s->st_c3_pairs;
+        local.pairs2_lost = s->st_lost2;
+        local.rounds_rebuilt = s->st_recovered;
         *stats = local;
     }
     return HTD_OK;

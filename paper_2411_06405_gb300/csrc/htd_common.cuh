@@ -58,6 +58,14 @@ struct DevStatus {
     int64_t st_tests;          // ball-membership tests of the support updates
     unsigned long long st_bytes_detect;  // algorithmic bytes, loss detection
     unsigned long long st_bytes_update;  // algorithmic bytes, incremental support updates
+    // incremental h = 3 rounds (radius-2 balls kept beside the radius-3 support balls)
+    int32_t nlost2;            // radius-2 lost-pair records of the current round
+    int32_t halt;              // 1: a round ran out of room; the host finishes it by rebuilds
+    long long nc3items;        // radius-3 candidate items of the current round (64-bit: the
+                               // reservations of a huge round may pass 2^31 before it halts)
+    int64_t st_c3_pairs;       // radius-3 candidate pairs tested
+    int64_t st_lost2;          // radius-2 lost pairs
+    int64_t st_recovered;      // rounds finished by the rebuild recovery
 };
 
 enum : int32_t {

@@ -69,6 +69,21 @@ struct PeelWork {
     int4 *uitems = nullptr;        // support update items (first slot, v, w, row end), <= 32 slots
     int64_t uitems_cap = 0;
     int64_t upd_budget = 0;        // adjacency slots one batch of updates may visit
+    // incremental h = 3: radius-2 balls (dense, x * Wpad) and their own metadata, used by
+    // the loss tests and by the rebuild that finishes a round which ran out of room
+    bool inc3 = false;
+    uint32_t *pool2 = nullptr;
+    int32_t *ball_size2 = nullptr;
+    int32_t *ball_nw2 = nullptr;
+    int2 *ball_meta2 = nullptr;
+    int32_t *changed_list2 = nullptr;
+    int32_t *changed_stamp2 = nullptr;
+    unsigned long long *lost2_keys = nullptr;  // hash set of the round's radius-2 lost pairs
+    int64_t lost2_cap = 0;
+    int64_t lost2_max = 0;
+    int4 *lost2 = nullptr;         // (min, max, hash slot, 0) per radius-2 lost pair
+    int4 *c3items = nullptr;       // radius-3 candidate items of a round
+    int64_t c3items_cap = 0;
     int32_t *bfs_lists = nullptr;  // per-block BFS level lists (h >= 3)
     int64_t bfs_list_len = 0;      // entries per list
     void *scan_tmp = nullptr;
@@ -117,7 +132,14 @@ htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent
 // Persistent kernel running up to max_slots incremental round slots (htd_loss.cu).
 htd_status launch_persistent_rounds(Handle *H, cudaStream_t s, int max_slots, int64_t *launches);
 
-// One incremental round (h <= 2) as four launches, the graph path (htd_loss.cu).
+// Finishes a round of the incremental h = 3 peel that ran out of room (status halt): its
+// frontier is already removed; the balls of every vertex within distance 2 of a frontier
+// endpoint are rebuilt and the supports of edges at changed balls recomputed (htd_peel.cu).
+htd_status recover_round_h3(Handle *H, cudaStream_t s, int64_t *launches);
+// Initial radius-2 balls of the incremental h = 3 peel (htd_peel.cu).
+htd_status initial_pass_r2(Handle *H, cudaStream_t s, int64_t *launches);
+
+// One incremental round (h <= 3) as four (h = 3: five) launches, the graph path (htd_loss.cu).
 htd_status enqueue_incremental_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t *evs,
                                      unsigned record_flags);
 

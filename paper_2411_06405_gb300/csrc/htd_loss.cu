@@ -76,6 +76,17 @@ struct LossArgs {
     int4 *uitems;
     long long upd_budget;
     DevStatus *st;
+    // h = 3: radius-2 balls and the round's radius-2 losses
+    int32_t h3;         // incremental h = 3 round: overflows halt the round (host rebuild)
+    int32_t rec_r2;     // this launch records radius-2 losses (no support updates)
+    uint32_t *pool2;    // dense radius-2 balls, row x at x * Wpad
+    int32_t *ball_size2;
+    unsigned long long *keys2;
+    unsigned long long cap2_mask;
+    int4 *lost2;
+    int32_t lost2_max;
+    int32_t c3items_cap;
+    int4 *c3items;
 };
 
 __device__ __forceinline__ unsigned long long pair_key(int p, int q) {
@@ -98,6 +109,18 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
 template <typename T>
 __device__ __forceinline__ T vload(const T &x) {
     return *(const volatile T *)&x;
+}
+
+// A batch limit was reached at edge side u: h <= 2 resumes the round there in the next slot;
+// an h = 3 round halts and the host finishes it by rebuilds.
+__device__ __forceinline__ void overflow_at(const LossArgs &a, DevStatus *st, int u) {
+    if (a.h3) atomicOr(&st->halt, 1);
+    else atomicMin(&st->overflow_unit, u);
+}
+
+// Round kernels do nothing once the peel is over or a round halted.
+__device__ __forceinline__ bool round_idle(const LossArgs &a) {
+    return vload(a.st->alive) == 0 || vload(a.st->halt) != 0;
 }
 
 // Alive-adjacency set of p if p has one (high degree), else null.
@@ -307,10 +330,19 @@ __device__ __forceinline__ void record_lost_warp(const LossArgs &a, DevStatus *s
                                                  int z, int u, unsigned &reads) {
     constexpr int kOwnItems = 8;
     const int lane = threadIdx.x & 31;
-    const bool want = lost && ball_contains(a, x, z, reads);
+    const bool r2 = a.rec_r2 != 0;  // radius-2 losses of an h = 3 round: record only
+    bool want = false;
+    if (lost) {
+        if (r2) {
+            reads++;
+            want = (a.pool2[(int64_t)x * a.Wpad + (z >> 5)] >> (z & 31)) & 1u;
+        } else {
+            want = ball_contains(a, x, z, reads);
+        }
+    }
     int rbx = 0, rex = 0, rbz = 0, rez = 0;
     long long work = 0;
-    if (want) {
+    if (want && !r2) {
         rbx = a.row_ptr[x];
         rex = a.row_ptr[x + 1];
         rbz = a.row_ptr[z];
@@ -325,34 +357,40 @@ __device__ __forceinline__ void record_lost_warp(const LossArgs &a, DevStatus *s
     long long wbase = 0;
     int ibase = 0;
     if (lane == 0) {
-        wbase = (long long)atomicAdd((unsigned long long *)&st->upd_work, (unsigned long long)wtot);
-        ibase = atomicAdd(&st->nlost, __popc(wantb));
+        if (!r2)
+            wbase = (long long)atomicAdd((unsigned long long *)&st->upd_work, (unsigned long long)wtot);
+        ibase = atomicAdd(r2 ? &st->nlost2 : &st->nlost, __popc(wantb));
     }
     wbase = __shfl_sync(0xffffffffu, wbase, 0);
     ibase = __shfl_sync(0xffffffffu, ibase, 0);
+    int4 *const lostv = r2 ? a.lost2 : a.lost;
+    unsigned long long *const keys = r2 ? a.keys2 : a.keys;
+    const unsigned long long cmask = r2 ? a.cap2_mask : a.cap_mask;
+    const int lmax = r2 ? a.lost2_max : a.lost_max;
     int rec_idx = -1;
     if (want) {
         const int idx = ibase + rank;
-        if (idx >= a.lost_max || wbase + wincl > a.upd_budget) {
-            atomicMin(&st->overflow_unit, u);
-            if (idx < a.lost_max) a.lost[idx] = make_int4(-1, -1, -1, 0);
+        if (idx >= lmax || (!r2 && wbase + wincl > a.upd_budget)) {
+            overflow_at(a, st, u);
+            if (idx < lmax) lostv[idx] = make_int4(-1, -1, -1, 0);
         } else {
             const unsigned long long key = pair_key(x, z);
-            unsigned long long slot = mix64(key) & a.cap_mask;
+            unsigned long long slot = mix64(key) & cmask;
             int4 rec = make_int4(-1, -1, -1, 0);  // null record: the pair is already held
-            for (unsigned long long probe = 0; probe <= a.cap_mask; probe++) {
-                const unsigned long long prev = atomicCAS(a.keys + slot, kEmpty, key);
+            for (unsigned long long probe = 0; probe <= cmask; probe++) {
+                const unsigned long long prev = atomicCAS(keys + slot, kEmpty, key);
                 if (prev == kEmpty) {
                     rec = make_int4(min(x, z), max(x, z), (int)slot, 0);
                     break;
                 }
                 if (prev == key) break;
-                slot = (slot + 1) & a.cap_mask;
+                slot = (slot + 1) & cmask;
             }
-            a.lost[idx] = rec;
+            lostv[idx] = rec;
             if (rec.x >= 0) rec_idx = idx;
         }
     }
+    if (r2) return;  // radius-2 losses change no support directly
     // update items: direction 0 = v0 = min loses v1, direction 1 = v1 loses v0
     int v0 = 0, v1 = 0, rb0 = 0, re0 = 0, rb1 = 0, re1 = 0, n0 = 0, n1 = 0;
     if (rec_idx >= 0) {
@@ -440,7 +478,7 @@ __device__ void ph_pair_items(const LossArgs &a) {
         base = __shfl_sync(0xffffffffu, base, 31);
         const int first = base + incl - nch;
         const bool fits = first + nch <= a.pitems_cap;
-        if (!fits && nch) atomicMin(&st->overflow_unit, u);
+        if (!fits && nch) overflow_at(a, st, u);
         // the whole warp writes each lane's items in turn (a hub row has hundreds)
         unsigned todo = __ballot_sync(0xffffffffu, nch > 0);
         while (todo) {
@@ -653,6 +691,262 @@ __device__ void ph_apply(const LossArgs &a) {
         atomicAdd((unsigned long long *)&st->st_recomputed, touched);
 }
 
+// ---- h = 3 -------------------------------------------------------------------------------
+//
+// At h = 3 the supports are taken on radius-3 balls B3 while radius-2 balls B2 are kept
+// beside them.  Removing F can only separate pairs that had a path of at most 3 edges
+// through a removed edge (a,b), i.e. pairs {p,q} with p in B(a,i), q in B(b,2-i) before the
+// removal, i = 0, 1, 2:  {a} x B2_old(b),  N_old(a) x N_old(b),  B2_old(a) x {b}.  A
+// candidate still in B3_old(p) stays within distance 3 iff q is in B2_new(z) for z = p or
+// for some alive neighbour z of p (or, symmetrically, of q).  B2_new is the stored B2 minus
+// this round's radius-2 losses, which the radius-2 detection (the h = 2 rule, recorded in
+// their own pair set) has listed first.  Radius-3 losses then take the support deltas of
+// the h = 2 rounds unchanged, on B3.
+
+// Is the pair {p,q} among this round's radius-2 losses?
+__device__ __forceinline__ bool lost2_now(const LossArgs &a, int p, int q, unsigned &bytes) {
+    const unsigned long long key = pair_key(p, q);
+    unsigned long long slot = mix64(key) & a.cap2_mask;
+    for (unsigned long long probe = 0; probe <= a.cap2_mask; probe++) {
+        const unsigned long long k = a.keys2[slot];
+        bytes += 8;
+        if (k == key) return true;
+        if (k == kEmpty) return false;
+        slot = (slot + 1) & a.cap2_mask;
+    }
+    return false;
+}
+
+// q in B2_new(z): the stored radius-2 bit, unless this round lost the pair.
+__device__ __forceinline__ bool in_b2_new(const LossArgs &a, int z, int q, unsigned &bytes) {
+    bytes += 4;
+    if (!((a.pool2[(int64_t)z * a.Wpad + (q >> 5)] >> (q & 31)) & 1u)) return false;
+    return z == q || !lost2_now(a, z, q, bytes);
+}
+
+// Words of a B2 row one radius-3 candidate item scans.
+constexpr int kC3Words = 512;
+
+// Radius-3 candidate items of the round's frontier, one warp per frontier edge (a,b):
+//   (a, row b, word range) and (b, row a, word range): {a} x B2_old(b) and {b} x B2_old(a);
+//   (p, row b, 32 slots) for every old neighbour p != b of a: N_old(a) x N_old(b).
+// Item layout: (x, y, first word | first slot, -1 - end word | end slot).
+__device__ void ph_c3_items(const LossArgs &a) {
+    DevStatus *st = a.st;
+    const int nF = vload(st->nF), round = vload(st->round);
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int nch = (a.Wpad + kC3Words - 1) / kC3Words;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nF; i += nwarps) {
+        const int e = a.frontier[i];
+        const int ea = a.eu[e], eb = a.ev[e];
+        long long base = 0;
+        if (lane == 0) base = (long long)atomicAdd((unsigned long long *)&st->nc3items,
+                                                   (unsigned long long)(2 * nch));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base + 2 * nch > a.c3items_cap) {
+            if (lane == 0) atomicOr(&st->halt, 1);
+        } else {
+            for (int c = lane; c < 2 * nch; c += 32) {
+                const int side = c / nch, ch = c % nch;
+                const int w0 = ch * kC3Words, w1 = min(a.Wpad, w0 + kC3Words);
+                a.c3items[base + c] = side ? make_int4(eb, ea, w0, -1 - w1) : make_int4(ea, eb, w0, -1 - w1);
+            }
+        }
+        const int rba = a.row_ptr[ea], rea = a.row_ptr[ea + 1];
+        const int rbb = a.row_ptr[eb], reb = a.row_ptr[eb + 1];
+        const int nb = (reb - rbb + 31) >> 5;
+        for (int s0 = rba; s0 < rea; s0 += 32) {
+            const int sl = s0 + lane;
+            int p = -1;
+            if (sl < rea) {
+                const int c = a.col[sl], cl = a.col_live[sl];
+                if (c != eb && (cl >= 0 || cl == -(round + 1))) p = c;
+            }
+            const int cnt = p >= 0 ? nb : 0;
+            const int incl = warp_incl_scan(cnt);
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            long long b2 = 0;
+            if (lane == 31 && tot)
+                b2 = (long long)atomicAdd((unsigned long long *)&st->nc3items, (unsigned long long)tot);
+            b2 = __shfl_sync(0xffffffffu, b2, 31);
+            if (b2 + tot > a.c3items_cap) {
+                if (lane == 0 && tot) atomicOr(&st->halt, 1);
+                continue;
+            }
+            const int first = (int)b2 + incl - cnt;
+            for (int c = 0; c < cnt; c++)
+                a.c3items[first + c] = make_int4(p, eb, rbb + 32 * c, min(reb, rbb + 32 * (c + 1)));
+        }
+    }
+}
+
+// Common walk of the warp's hard radius-3 pairs (lanes with state == kHard): w is the
+// endpoint whose alive row is walked, t the other one; the pair is kept at the first alive
+// neighbour y of w with t in B2_new(y).  The rows are laid end to end and walked 128 slots
+// per step as in warp_hard_pairs.  Called by whole warps.
+__device__ __forceinline__ void warp_walk3(const LossArgs &a, int &state, int w, int t,
+                                           unsigned &reads) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool hard = state == kHard;
+    int rb = 0, len = 0;
+    if (hard) {
+        rb = a.row_ptr[w];
+        len = a.row_ptr[w + 1] - rb;
+        reads += 2;
+    }
+    const int incl = warp_incl_scan(len);
+    const int excl = incl - len;
+    const int total = __shfl_sync(full, incl, 31);
+    unsigned pending = __ballot_sync(full, hard);
+    unsigned kept = 0u;
+    for (int base = 0; base < total && pending; base += 128) {
+        int y[4], own[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int idx = base + 32 * j + lane;
+            int o = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(full, incl, o + step - 1) <= idx) o += step;
+            o = min(o, 31);
+            const int ex = __shfl_sync(full, excl, o), rbo = __shfl_sync(full, rb, o);
+            own[j] = o;
+            y[j] = (idx < total && ((pending >> o) & 1u)) ? a.col_live[rbo + idx - ex] : -1;
+        }
+        unsigned hits = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int to = __shfl_sync(full, t, own[j]);
+            if (y[j] >= 0) {
+                reads++;
+                if (in_b2_new(a, y[j], to, reads)) hits |= 1u << own[j];
+            }
+        }
+        hits = __reduce_or_sync(full, hits);
+        kept |= hits;
+        pending &= ~hits;
+    }
+    if (hard) state = ((kept >> lane) & 1u) ? kKept : kLost;
+}
+
+// Tests the lanes' radius-3 candidate pairs {p,q} (q < 0: none; q is in B3_old(p)) in the
+// new graph and records the lost ones with their support-update items.  Whole warps.
+__device__ __forceinline__ void test_pairs3(const LossArgs &a, DevStatus *st, int p, int q,
+                                            unsigned &reads, unsigned long long &pairs) {
+    int state = kKept, w = p, t = q;
+    if (q >= 0) {
+        pairs++;
+        if (!in_b2_new(a, p, q, reads)) {
+            state = kHard;
+            reads += 2;
+            if (a.deg_alive[q] < a.deg_alive[p]) {  // walk the shorter alive row
+                w = q;
+                t = p;
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, state == kHard)) warp_walk3(a, state, w, t, reads);
+    record_lost_warp(a, st, state == kLost, p, q, 0, reads);
+}
+
+// Radius-3 loss tests, one warp per candidate item.
+__device__ void ph_test3(const LossArgs &a) {
+    __shared__ unsigned long long s_pairs, s_reads;
+    DevStatus *st = a.st;
+    if (threadIdx.x == 0) {
+        s_pairs = 0ull;
+        s_reads = 0ull;
+    }
+    __syncthreads();
+    const int nitems = (int)min(vload(st->nc3items), (long long)a.c3items_cap);
+    const int round = vload(st->round);
+    const int lane = threadIdx.x & 31;
+    unsigned long long pairs = 0ull, reads_total = 0ull;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nwarps) {
+        const int4 item = a.c3items[it];
+        const int x = item.x, y = item.y;
+        unsigned reads = 0;
+        if (item.w < 0) {
+            // {x} x B2_old(y), restricted to B3_old(x): one pair per lane at a time
+            const int w1 = -1 - item.w;
+            const uint32_t *r2 = a.pool2 + (int64_t)y * a.Wpad;
+            const uint32_t *r3 = a.pool + (int64_t)x * a.Wpad;
+            int wi = item.z + lane;
+            uint32_t bits = 0u;
+            int wbase = 0;
+            for (;;) {
+                while (bits == 0u && wi < w1) {
+                    bits = r2[wi] & r3[wi];
+                    reads += 2;
+                    if (wi == (x >> 5)) bits &= ~(1u << (x & 31));
+                    wbase = wi << 5;
+                    wi += 32;
+                }
+                const bool has = bits != 0u;
+                if (!__any_sync(0xffffffffu, has)) break;
+                int q = -1;
+                if (has) {
+                    q = wbase + __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                }
+                test_pairs3(a, st, x, q, reads, pairs);
+            }
+        } else {
+            // {x} x N_old(y) for the slots of the item, restricted to B3_old(x)
+            const int sl = item.z + lane;
+            int q = -1;
+            if (sl < item.w) {
+                const int c = a.col[sl], cl = a.col_live[sl];
+                reads += 2;
+                if (c != x && (cl >= 0 || cl == -(round + 1))) {
+                    reads++;
+                    if ((a.pool[(int64_t)x * a.Wpad + (c >> 5)] >> (c & 31)) & 1u) q = c;
+                }
+            }
+            test_pairs3(a, st, x, q, reads, pairs);
+        }
+        reads_total += reads;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        reads_total += __shfl_xor_sync(0xffffffffu, reads_total, o);
+    }
+    if (lane == 0 && pairs) {
+        atomicAdd(&s_pairs, pairs);
+        atomicAdd(&s_reads, reads_total);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_pairs) {
+        atomicAdd((unsigned long long *)&st->st_c3_pairs, s_pairs);
+        atomicAdd(&st->st_bytes_detect, 4ull * s_reads);
+    }
+}
+
+// Clears the round's radius-2 losses from the stored B2 (and their pair-set slots).
+__device__ void ph_apply2(const LossArgs &a) {
+    DevStatus *st = a.st;
+    const int nlost = min(vload(st->nlost2), a.lost2_max);
+    unsigned long long real = 0ull;
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < 2 * nlost; d += gridDim.x * blockDim.x) {
+        const int4 L = a.lost2[d >> 1];
+        if (L.x < 0) continue;
+        const int v = (d & 1) ? L.y : L.x;
+        const int w = (d & 1) ? L.x : L.y;
+        const uint32_t bit = 1u << (w & 31);
+        const uint32_t old = atomicAnd(a.pool2 + (int64_t)v * a.Wpad + (w >> 5), ~bit);
+        if (old & bit) atomicSub(a.ball_size2 + v, 1);
+        if ((d & 1) == 0) {
+            a.keys2[L.z] = kEmpty;
+            real++;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) real += __shfl_xor_sync(0xffffffffu, real, o);
+    if ((threadIdx.x & 31) == 0 && real) atomicAdd((unsigned long long *)&st->st_lost2, real);
+}
+
 // Phase 1 of an incremental round: every alive edge with h-support <= k-2 joins F and is
 // removed at once (Algorithm 1, lines 7-10), and the loss detection items of its two edge
 // sides are written.  A continued round only writes the items of its remaining sides.
@@ -710,8 +1004,8 @@ __device__ void ph_select_items(const LossArgs &a) {
             if (lane == 31 && tot) ibase = atomicAdd(&st->npitems, tot);
             ibase = __shfl_sync(0xffffffffu, ibase, 31);
             const int first = ibase + incl - (n0 + n1);
-            if (p && first + n0 > a.pitems_cap) atomicMin(&st->overflow_unit, 2 * pos);
-            if (p && n1 && first + n0 + n1 > a.pitems_cap) atomicMin(&st->overflow_unit, 2 * pos + 1);
+            if (p && first + n0 > a.pitems_cap) overflow_at(a, st, 2 * pos);
+            if (p && n1 && first + n0 + n1 > a.pitems_cap) overflow_at(a, st, 2 * pos + 1);
             unsigned todo = __ballot_sync(0xffffffffu, p);
             while (todo) {
                 const int l = __ffs(todo) - 1;
@@ -747,23 +1041,31 @@ __device__ __forceinline__ void phase_entry() {
 // One launch per phase (the rounds of a CUDA graph).
 __global__ void __launch_bounds__(kBlock) k_inc_select(LossArgs a) {
     phase_entry();
-    if (vload(a.st->alive) == 0) return;
+    if (round_idle(a)) return;
     ph_select_items(a);
 }
+// h = 3: the radius-2 detection (a.rec_r2) and the round's radius-3 candidate items
 __global__ void __launch_bounds__(kBlock) k_loss_detect(LossArgs a) {
     phase_entry();
-    if (vload(a.st->alive) == 0) return;
+    if (round_idle(a)) return;
     ph_detect(a);
+    if (a.h3) ph_c3_items(a);
+}
+__global__ void __launch_bounds__(kBlock) k_loss3_test(LossArgs a) {
+    phase_entry();
+    if (round_idle(a)) return;
+    ph_test3(a);
 }
 __global__ void __launch_bounds__(kBlock) k_loss_delta(LossArgs a) {
     phase_entry();
-    if (vload(a.st->alive) == 0) return;
+    if (round_idle(a)) return;
     ph_delta(a);
 }
 __global__ void __launch_bounds__(kBlock) k_loss_apply_reduce(LossArgs a) {
     phase_entry();
-    if (vload(a.st->alive) == 0) return;
+    if (round_idle(a)) return;
     ph_apply(a);
+    if (a.h3) ph_apply2(a);
     minreduce_body<kBlock / 32>(a.sup, a.m, a.st, 0);
 }
 
@@ -853,6 +1155,16 @@ LossArgs loss_args(Handle *H) {
     a.deg_alive_w = w.deg_alive;
     a.hub_bits_w = w.hub_bits;
     a.st = w.status;
+    a.h3 = w.inc3 ? 1 : 0;
+    a.rec_r2 = 0;
+    a.pool2 = w.pool2;
+    a.ball_size2 = w.ball_size2;
+    a.keys2 = w.lost2_keys;
+    a.cap2_mask = w.lost2_cap > 0 ? (unsigned long long)(w.lost2_cap - 1) : 0ull;
+    a.lost2 = w.lost2;
+    a.lost2_max = (int32_t)w.lost2_max;
+    a.c3items_cap = (int32_t)w.c3items_cap;
+    a.c3items = w.c3items;
     return a;
 }
 
@@ -890,20 +1202,22 @@ namespace {
 // Blocks of one full wave of a phase kernel (every block resident at once), per device.
 struct PhaseGrids {
     int device = -1;
-    int detect = 0, delta = 0;
+    int detect = 0, delta = 0, test3 = 0;
 };
 
 htd_status phase_grids(Handle *H, PhaseGrids &pg) {
     if (pg.device == H->g.device) return HTD_OK;
-    int od = 0, ou = 0;
+    int od = 0, ou = 0, ot = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, k_loss_detect, kBlock, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_loss_delta, kBlock, 0) != cudaSuccess ||
-        od < 1 || ou < 1) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ot, k_loss3_test, kBlock, 0) != cudaSuccess ||
+        od < 1 || ou < 1 || ot < 1) {
         set_last_error("incremental round: no resident block fits");
         return HTD_ECUDA;
     }
     pg.detect = H->num_sms * od;
     pg.delta = H->num_sms * ou;
+    pg.test3 = H->num_sms * ot;
     pg.device = H->g.device;
     return HTD_OK;
 }
@@ -944,18 +1258,37 @@ htd_status enqueue_incremental_round(Handle *H, cudaStream_t s, int64_t *launche
     // hit the same few counters
     const int grid_scan = H->num_sms * 2;
     cudaError_t e = cudaSuccess;
-    mark(0);
-    if (e == cudaSuccess) e = launch_phase(k_inc_select, grid_scan, s, pdl, a);
-    mark(1);
-    mark(2);
-    if (e == cudaSuccess) e = launch_phase(k_loss_detect, pg.detect, s, pdl, a);
-    mark(3);
-    if (e == cudaSuccess) e = launch_phase(k_loss_delta, pg.delta, s, pdl, a);
-    mark(4);
-    mark(5);
-    if (e == cudaSuccess) e = launch_phase(k_loss_apply_reduce, grid_scan, s, pdl, a);
-    mark(6);
-    *launches += 4;
+    if (a.h3) {
+        // select | radius-2 detection + radius-3 items | radius-3 tests | updates | - | reduce
+        LossArgs a2 = a;
+        a2.rec_r2 = 1;
+        mark(0);
+        if (e == cudaSuccess) e = launch_phase(k_inc_select, grid_scan, s, pdl, a);
+        mark(1);
+        if (e == cudaSuccess) e = launch_phase(k_loss_detect, pg.detect, s, pdl, a2);
+        mark(2);
+        if (e == cudaSuccess) e = launch_phase(k_loss3_test, pg.test3, s, pdl, a);
+        mark(3);
+        if (e == cudaSuccess) e = launch_phase(k_loss_delta, pg.delta, s, pdl, a);
+        mark(4);
+        mark(5);
+        if (e == cudaSuccess) e = launch_phase(k_loss_apply_reduce, grid_scan, s, pdl, a);
+        mark(6);
+        *launches += 5;
+    } else {
+        mark(0);
+        if (e == cudaSuccess) e = launch_phase(k_inc_select, grid_scan, s, pdl, a);
+        mark(1);
+        mark(2);
+        if (e == cudaSuccess) e = launch_phase(k_loss_detect, pg.detect, s, pdl, a);
+        mark(3);
+        if (e == cudaSuccess) e = launch_phase(k_loss_delta, pg.delta, s, pdl, a);
+        mark(4);
+        mark(5);
+        if (e == cudaSuccess) e = launch_phase(k_loss_apply_reduce, grid_scan, s, pdl, a);
+        mark(6);
+        *launches += 4;
+    }
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_last_error(std::string("enqueue_incremental_round: ") + cudaGetErrorString(e));

@@ -456,8 +456,11 @@ __global__ void k_cand_init(const int32_t *__restrict__ frontier, const int32_t 
 
 // Depth d of the candidate search (alive edges, frontier still present): one warp per
 // vertex found at depth d-1.
+// with_removed: also follow the slots removed in the current round (the pre-removal graph
+// after the round's frontier is already gone: the h = 3 recovery).
 __global__ void k_cand_expand(int32_t d, const int32_t *__restrict__ row_ptr,
-                              const int32_t *__restrict__ col_live, DevStatus *st,
+                              const int32_t *__restrict__ col, const int32_t *__restrict__ col_live,
+                              int32_t with_removed, DevStatus *st,
                               int32_t *__restrict__ cand_stamp, int32_t *__restrict__ cand_list) {
     if (st->alive == 0) return;
     int start = 0;
@@ -472,7 +475,8 @@ __global__ void k_cand_expand(int32_t d, const int32_t *__restrict__ row_ptr,
         const int rb = row_ptr[w], re = row_ptr[w + 1];
         for (int s0 = rb; s0 < re; s0 += 32) {
             const int s = s0 + lane;
-            const int z = (s < re) ? col_live[s] : -1;
+            int z = (s < re) ? col_live[s] : -1;
+            if (with_removed && s < re && z == -(round + 1)) z = col[s];
             cand_mark(z >= 0, z >= 0 ? z : 0, round, d, out_base, cand_stamp, cand_list, st);
         }
     }
@@ -618,6 +622,15 @@ void free_work(PeelWork *w) {
     cudaFree(w->pitems);
     cudaFree(w->uitems);
     cudaFree(w->scan_tmp);
+    cudaFree(w->pool2);
+    cudaFree(w->ball_size2);
+    cudaFree(w->ball_nw2);
+    cudaFree(w->ball_meta2);
+    cudaFree(w->changed_list2);
+    cudaFree(w->changed_stamp2);
+    cudaFree(w->lost2_keys);
+    cudaFree(w->lost2);
+    cudaFree(w->c3items);
     cudaFree(w->status);
     if (w->status_host) cudaFreeHost(w->status_host);
     *w = PeelWork{};
@@ -627,9 +640,10 @@ void free_work(PeelWork *w) {
 htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) {
     PeelWork &w = H->w;
     GraphDev &g = H->g;
-    incremental = incremental && h <= 2;
+    incremental = incremental && h <= 3;
     if (w.status && w.h == h && (!incremental || (w.lost_keys && w.lost_tiny == tiny_table))) {
         w.incremental = incremental;
+        w.inc3 = incremental && h == 3;
         return HTD_OK;
     }
     if (w.status) {
@@ -687,8 +701,10 @@ htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) 
     if (incremental) {
         // a round's lost pairs: half of a power-of-two table of 8 x (2m) slots (>= 2^12)
         // sized to stay L2-resident (at most 2^22 slots, 32 MiB); larger rounds run in batches
+        // h = 3 rounds lose many more radius-3 pairs: a table up to 2^24 slots
+        const int64_t cap_max = (int64_t)1 << (h == 3 ? 24 : 22);
         int64_t cap = 4096;
-        while (cap < 4 * m && cap < ((int64_t)1 << 22)) cap <<= 1;
+        while (cap < 4 * m * (h == 3 ? 4 : 1) && cap < cap_max) cap <<= 1;
         if (tiny_table) cap = 128;  // forces rounds to run in many batches
         w.lost_tiny = tiny_table;
         w.lost_cap = cap;
@@ -704,6 +720,26 @@ htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) 
         w.uitems_cap = 2 * w.lost_max + w.upd_budget / 32 + 1024;
         HTD_CHECK(alloc_n(&w.pitems, w.pitems_cap));
         HTD_CHECK(alloc_n(&w.uitems, w.uitems_cap));
+        if (h == 3) {
+            // radius-2 balls (dense) with their own metadata, the round's radius-2 losses and
+            // the radius-3 candidate items
+            HTD_CHECK(alloc_n(&w.pool2, n * (int64_t)w.Wpad));
+            HTD_CHECK(alloc_n(&w.ball_size2, n));
+            HTD_CHECK(alloc_n(&w.ball_nw2, n));
+            HTD_CHECK(alloc_n(&w.ball_meta2, n));
+            HTD_CHECK(alloc_n(&w.changed_list2, n));
+            HTD_CHECK(alloc_n(&w.changed_stamp2, n));
+            int64_t cap2 = 4096;
+            while (cap2 < 4 * m && cap2 < ((int64_t)1 << 22)) cap2 <<= 1;
+            if (tiny_table) cap2 = 128;
+            w.lost2_cap = cap2;
+            w.lost2_max = cap2 / 2;
+            HTD_CHECK(alloc_n(&w.lost2_keys, cap2));
+            HTD_CHECK(alloc_n(&w.lost2, w.lost2_max));
+            w.c3items_cap = tiny_table ? 256
+                                       : std::min<int64_t>((int64_t)1 << 25, std::max<int64_t>(1 << 16, 8 * m));
+            HTD_CHECK(alloc_n(&w.c3items, w.c3items_cap));
+        }
         // alive-adjacency n-bit sets: every vertex of degree >= T, the smallest power of two
         // for which they fit in min(16 GiB, a quarter of the free device memory)
         std::vector<int32_t> rp(n + 1);
@@ -737,6 +773,7 @@ htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) 
         }
     }
     w.incremental = incremental;
+    w.inc3 = incremental && h == 3;
     HTD_CHECK(cudaMalloc(&w.scan_tmp, scan_temp_bytes(n + 1)));
     HTD_CHECK(alloc_n(&w.status, 1));
     HTD_CHECK(cudaMallocHost(reinterpret_cast<void **>(&w.status_host), sizeof(DevStatus)));
@@ -765,6 +802,10 @@ htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
     if (w.incremental) {
         HTD_CHECK(cudaMemsetAsync(w.edge_touch, 0xff, (n > 0 ? n : 1) * sizeof(int32_t), s));
         HTD_CHECK(cudaMemsetAsync(w.lost_keys, 0xff, w.lost_cap * sizeof(unsigned long long), s));
+        if (w.inc3) {
+            HTD_CHECK(cudaMemsetAsync(w.lost2_keys, 0xff, w.lost2_cap * sizeof(unsigned long long), s));
+            HTD_CHECK(cudaMemsetAsync(w.changed_stamp2, 0xff, (n > 0 ? n : 1) * sizeof(int32_t), s));
+        }
         if (w.nhub > 0) {
             k_hub_init<<<std::min(w.nhub, H->num_sms * 8), kBlock, 0, s>>>(w.hub_list, w.nhub, g.row_ptr,
                                                                         g.col, w.hub_bits, w.Wpad);
@@ -871,8 +912,8 @@ htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent
     k_cand_init<<<gsmall, kBlock, 0, s>>>(w.frontier, g.eu, g.ev, w.status, w.cand_stamp, w.cand_list);
     *launches += 2;
     for (int d = 1; d < w.h; d++) {
-        k_cand_expand<<<gsmall * 2, kBlock, 0, s>>>(d, g.row_ptr, w.col_live, w.status, w.cand_stamp,
-                                                     w.cand_list);
+        k_cand_expand<<<gsmall * 2, kBlock, 0, s>>>(d, g.row_ptr, g.col, w.col_live, 0, w.status,
+                                                     w.cand_stamp, w.cand_list);
         (*launches)++;
     }
     mark(2);
@@ -891,6 +932,103 @@ htd_status enqueue_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent
     k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, m, w.status, 0);
     mark(6);
     *launches += 4;
+    HTD_CHECK(cudaGetLastError());
+    return HTD_OK;
+}
+
+// Radius-2 balls of every vertex for the incremental h = 3 peel, stored dense in pool2
+// with their own sizes (the radius-3 balls and supports come from initial_pass).
+htd_status initial_pass_r2(Handle *H, cudaStream_t s, int64_t *launches) {
+    PeelWork &w = H->w;
+    if (!w.inc3 || H->g.n == 0) return HTD_OK;
+    BallArgs b2 = ball_args(H);
+    b2.h = 2;
+    b2.count_bytes = 0;
+    b2.force_dense = 1;
+    b2.pool = w.pool2;
+    b2.ball_size = w.ball_size2;
+    b2.ball_nw = w.ball_nw2;
+    b2.ball_meta = w.ball_meta2;
+    b2.changed_list = w.changed_list2;
+    b2.changed_stamp = w.changed_stamp2;
+    b2.bfs_lists = nullptr;
+    HTD_CHECK(cudaMemsetAsync(&w.status->q_store, 0, sizeof(int32_t), s));
+    k_ball<kModeStore><<<w.grid_ball, kBlock, w.smem_ball, s>>>(b2);
+    (*launches)++;
+    HTD_CHECK(cudaGetLastError());
+    return HTD_OK;
+}
+
+namespace {
+
+// Clears what a halted h = 3 round recorded (its pair sets are emptied by the caller) and
+// the queue heads the rebuild kernels use.
+__global__ void k_recover_reset(DevStatus *st) {
+    st->halt = 0;
+    st->nlost = 0;
+    st->nlost2 = 0;
+    st->npitems = 0;
+    st->nuitems = 0;
+    st->nc3items = 0;
+    st->upd_work = 0;
+    st->overflow_unit = INT_MAX;
+    for (int j = 0; j < kMaxH; j++) st->cand_cnt[j] = 0;
+    st->q_ball = 0;
+    st->nchanged = 0;
+    st->nitems = 0;
+    st->q_items = 0;
+    st->st_recovered++;
+}
+
+__global__ void k_reset_rebuild_queue(DevStatus *st) {
+    st->q_ball = 0;
+    st->nchanged = 0;
+}
+
+}  // namespace
+
+// Finishes a halted round of the incremental h = 3 peel.  Its frontier is already removed
+// (slots marked with the round) and nothing else of the round was applied: balls and
+// supports are those of before the round.  Every vertex within distance 2 of a frontier
+// endpoint in the pre-removal graph is a candidate: its radius-2 ball (if within distance
+// 1) and its radius-3 ball are rebuilt, and the supports of the alive edges at vertices
+// whose radius-3 ball shrank are recomputed; the min reduction then closes the round.
+htd_status recover_round_h3(Handle *H, cudaStream_t s, int64_t *launches) {
+    PeelWork &w = H->w;
+    GraphDev &g = H->g;
+    const int gsmall = H->num_sms * 4;
+    HTD_CHECK(cudaMemsetAsync(w.lost_keys, 0xff, w.lost_cap * sizeof(unsigned long long), s));
+    HTD_CHECK(cudaMemsetAsync(w.lost2_keys, 0xff, w.lost2_cap * sizeof(unsigned long long), s));
+    k_recover_reset<<<1, 1, 0, s>>>(w.status);
+    k_cand_init<<<gsmall, kBlock, 0, s>>>(w.frontier, g.eu, g.ev, w.status, w.cand_stamp, w.cand_list);
+    *launches += 2;
+    for (int d = 1; d < 3; d++) {
+        k_cand_expand<<<gsmall * 2, kBlock, 0, s>>>(d, g.row_ptr, g.col, w.col_live, 1, w.status,
+                                                     w.cand_stamp, w.cand_list);
+        (*launches)++;
+    }
+    // radius 2: candidates of depth 0..1 (the rebuild counts the first h levels)
+    BallArgs b2 = ball_args(H);
+    b2.h = 2;
+    b2.count_bytes = 0;
+    b2.force_dense = 1;
+    b2.pool = w.pool2;
+    b2.ball_size = w.ball_size2;
+    b2.ball_nw = w.ball_nw2;
+    b2.ball_meta = w.ball_meta2;
+    b2.changed_list = w.changed_list2;
+    b2.changed_stamp = w.changed_stamp2;
+    b2.bfs_lists = nullptr;
+    k_ball<kModeRebuild><<<w.grid_ball, kBlock, w.smem_ball, s>>>(b2);
+    k_reset_rebuild_queue<<<1, 1, 0, s>>>(w.status);
+    // radius 3 and the supports it changes
+    BallArgs b3 = ball_args(H);
+    k_ball<kModeRebuild><<<w.grid_ball, kBlock, w.smem_ball, s>>>(b3);
+    k_make_items<<<gsmall, kBlock, 0, s>>>(w.changed_list, 0, g.n, g.row_ptr, w.items, w.status);
+    HsupArgs ha = hsup_args(H, 0);
+    k_hsup<<<w.grid_hsup, kBlock, w.smem_hsup, s>>>(ha);
+    k_minreduce<<<w.grid_edges, kBlock, 0, s>>>(w.sup, g.m, w.status, 0);
+    *launches += 6;
     HTD_CHECK(cudaGetLastError());
     return HTD_OK;
 }

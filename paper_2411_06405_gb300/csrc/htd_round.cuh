@@ -72,6 +72,8 @@ __device__ __forceinline__ void round_finalize(DevStatus *st, int initial) {
     for (int j = 0; j < kMaxH; j++) st->cand_cnt[j] = 0;
     st->nchanged = 0;
     st->nlost = 0;
+    st->nlost2 = 0;
+    st->nc3items = 0;
     st->npitems = 0;
     st->nuitems = 0;
     st->upd_work = 0;

@@ -15,5 +15,6 @@ from .generators import (  # noqa: F401
     dcsbm,
     erdos_renyi_gnm,
     rmat,
+    served_requests,
     small_corpus,
 )

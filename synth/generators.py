@@ -274,6 +274,33 @@ def batch_graphs(count: int, seed: int, n_lo: int = 50, n_hi: int = 5000):
     return out
 
 
+def served_requests(count: int, seed: int, rate: float = 200.0, rmat_scales=(10, 20),
+                    ba_n=(1_000, 1_000_000)):
+    """A Poisson request stream over a mixed pool: arrival times with exponential gaps of
+    mean 1/rate seconds; each request is, with equal odds, an R-MAT graph (scale uniform in
+    rmat_scales, edge factor 8, (0.57,0.19,0.19,0.05)) or a Barabasi-Albert graph (n
+    log-uniform in ba_n, m0 ~ U{2..8}), with h ~ U{2,3}.  Request i draws its graph from
+    sub-seed seed ^ i.  Returns a list of (arrival_s, n, src, dst, h, kind)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        sub = seed ^ i
+        h = int(rng.integers(2, 4))
+        if rng.random() < 0.5:
+            sc = int(rng.integers(rmat_scales[0], rmat_scales[1] + 1))
+            s, d = rmat(sc, 8, 0.57, 0.19, 0.19, sub)
+            out.append((t, 1 << sc, s, d, h, f"rmat_s{sc}"))
+        else:
+            lo, hi = np.log(ba_n[0]), np.log(ba_n[1])
+            n = int(round(np.exp(rng.uniform(lo, hi))))
+            m0 = int(rng.integers(2, 9))
+            s, d = barabasi_albert(max(n, m0 + 1), m0, sub)
+            out.append((t, max(n, m0 + 1), s, d, h, f"ba_n{n}_m{m0}"))
+    return out
+
+
 def small_corpus(count: int, seed: int, max_n: int = 40):
     """Mixed small graphs (ER, BA, R-MAT) for bulk parity checks: yields (n, src, dst)."""
     rng = np.random.default_rng(seed)

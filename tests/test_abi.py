@@ -52,6 +52,43 @@ def test_stats_struct_matches_header(lib):
     assert [(n, ctype[t]) for t, n in fields] == list(_lib.HtdStats._fields_)
 
 
+def _struct_fields(name):
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    ctype = {"int64_t": ctypes.c_int64, "int32_t": ctypes.c_int32, "double": ctypes.c_double,
+             "float": ctypes.c_float}
+    return [(n, ctype[t]) for t, n in re.findall(r"(int64_t|int32_t|double|float)\s+(\w+);", body)]
+
+
+def test_server_structs_match_header(lib):
+    from paper_2411_06405_gb300 import _lib
+
+    assert _struct_fields("htd_request_info") == list(_lib.HtdRequestInfo._fields_)
+    assert _struct_fields("htd_server_stats") == list(_lib.HtdServerStats._fields_)
+
+
+def test_footprint_estimate_on_host(lib):
+    # host-only: grows with the graph, dense balls when they fit a quarter of free memory
+    est = [lib.htd_footprint_estimate(n, 8 * n, 2, 200 << 30) for n in (1000, 10000, 100000)]
+    assert est[0] < est[1] < est[2]
+    small_free = lib.htd_footprint_estimate(100000, 800000, 2, 1 << 30)
+    assert small_free < est[2]  # compact estimate when the dense sets do not fit
+    assert lib.htd_footprint_estimate(1000, 8000, 3, 200 << 30) > est[0]  # two ball radii
+    assert lib.htd_footprint_estimate(-1, 0, 2, 0) == -1
+
+
+def test_server_rejects_bad_arguments_without_a_device(lib):
+    out = ctypes.c_void_p()
+    assert lib.htd_server_create(0, 0, 0, ctypes.byref(out)) == 1
+    assert lib.htd_server_create(4, -5, 0, ctypes.byref(out)) == 1
+    rid = ctypes.c_int64()
+    assert lib.htd_server_submit(None, 4, None, None, 0, 2, ctypes.byref(rid)) == 1
+    done = ctypes.c_int32()
+    assert lib.htd_server_poll(None, 1, ctypes.byref(done)) == 1
+    lib.htd_server_destroy(None)
+
+
 def test_status_strings(lib):
     for code in range(7):
         assert lib.htd_status_string(code)

@@ -148,7 +148,10 @@ def test_truss_corpus(htd, oracle_mod, h, mode):
         t, _, st = htd.htd_truss_decompose(g, h, flags=MODES[mode])
         np.testing.assert_array_equal(host(t), og.truss_decompose(h)[0])
         if g.m:
-            assert st["incremental"] == (1 if (h <= 2 and mode != "rebuild") else 0)
+            # h = 3 rounds are incremental on dense balls only; h >= 4 rebuilds
+            inc = (h <= 2 and mode != "rebuild") or (h == 3 and mode in ("incremental",
+                                                                          "persistent"))
+            assert st["incremental"] == (1 if inc else 0)
 
 
 @pytest.mark.parametrize("mode", sorted(MODES))
@@ -264,6 +267,20 @@ def test_host_entry_point(htd, oracle_mod):
 
 # ---- full-size workloads (the benchmark's launch configuration) ---------------------------------
 
+def test_incremental_h3_matches_rebuild_on_hubby_graph(htd):
+    # R-MAT scale 12 at h = 3: hub balls cover most of the graph; incremental rounds (with
+    # and without forced rebuild finishes) and rebuild rounds must agree exactly, stamps too
+    s, d = rmat(12, 8, 0.57, 0.19, 0.19, 98)
+    g = gpu_graph(htd, 1 << 12, s, d)
+    a, sa, st_a = htd.htd_truss_decompose(g, 3, stamps=True)
+    b, sb, st_b = htd.htd_truss_decompose(g, 3, stamps=True, flags=htd.HTD_OPT_REBUILD)
+    c, sc, st_c = htd.htd_truss_decompose(g, 3, stamps=True, flags=htd.HTD_OPT_TINY_LOSS_TABLE)
+    assert st_a["incremental"] == 1 and st_b["incremental"] == 0 and st_c["incremental"] == 1
+    assert st_a["pairs3_tested"] > 0 and st_c["rounds_rebuilt"] > 0
+    assert torch.equal(a, b) and torch.equal(sa, sb)
+    assert torch.equal(a, c) and torch.equal(sa, sc)
+
+
 def test_incremental_matches_rebuild_on_hubby_graph(htd):
     # R-MAT scale 13: hubs, thousands of rounds; both round variants must agree exactly
     s, d = rmat(13, 8, 0.57, 0.19, 0.19, 99)
@@ -298,7 +315,7 @@ def test_ball_layout_switch_on_one_handle(htd, oracle_mod):
             np.testing.assert_array_equal(host(t), ref, err_msg=f"h={h} flags={flags}")
 
 
-@pytest.mark.parametrize("h", [1, 2])
+@pytest.mark.parametrize("h", [1, 2, 3])
 def test_batched_rounds_match_oracle(htd, oracle_mod, h):
     # a 128-slot lost-pair table splits most rounds into many batches
     for (n, (s, d)) in ((512, rmat(9, 8, 0.57, 0.19, 0.19, 61)),
@@ -317,6 +334,9 @@ def test_batched_rounds_match_oracle(htd, oracle_mod, h):
         np.testing.assert_array_equal(host(t), t_ref)
         np.testing.assert_array_equal(host(stamp), stamp_ref)  # same rounds as the oracle
         assert st["rounds"] == rounds and st["incremental"] == 1
+        if h == 3:
+            # 128-slot tables: most h = 3 rounds halt and are finished by rebuilds
+            assert st["rounds_rebuilt"] > 0
 
 
 @pytest.mark.slow
