@@ -252,6 +252,38 @@ htd_status htd_h_support_static(int32_t n, const int32_t *row_ptr_dev, const int
                                 int64_t m, const int32_t *eu_dev, const int32_t *ev_dev,
                                 int32_t h, int32_t *sup_dev, void *stream);
 
+/* ---- The paper's own parallel method: the higher-order H-index iteration (Sec. 4) -----
+ *
+ * H^(0)(e) = sup(e,h); order n sets, for every edge e = (u,v),
+ *   H^(n)(e) = H({ min(P(u,w), P(v,w)) : w in N(u,h) ∩ N(v,h) }),
+ * H(S) the largest y with at least y members of S >= y, and P(a,b) the h-hop reachable path
+ * key: the largest, over paths from a to b of at most h edges, of the smallest H^(n-1) on
+ * the path (Definition of the h-hop reachable path key; Algorithm 2).  Keys never increase
+ * (Theorem 3) and stop at t(e,h) - 2 (Theorem 4).  Paths may use e itself; the common
+ * h-neighbourhood is that of the whole graph. */
+typedef struct htd_hindex_stats {
+    int64_t ball_entries;    /* sum of the closed h-hop ball sizes (stored member lists) */
+    int64_t kernel_launches;
+    int32_t h;
+    int32_t sweeps;          /* sub-sweeps per order (1 = synchronous) */
+    int32_t iterations;      /* orders computed (the last one changed nothing if converged) */
+    int32_t converged;
+    float ms_total;          /* device time of the call (CUDA events) */
+    int32_t pad;
+} htd_hindex_stats;
+
+/* Runs the H-index iteration from H^(0) = sup(e,h) until an order changes nothing (or for
+ * max_iter orders, max_iter >= 0).  sweeps = 1: synchronous orders, each computed from the
+ * previous order only (Algorithm 2).  sweeps = S > 1: asynchronous updating by blocks of
+ * edges: each order is S sub-sweeps over consecutive edge-id ranges, each using the keys
+ * already updated by the sub-sweeps before it.  Outputs (device, m int32 each, nullable):
+ * truss_dev = H + 2 (the h-trussness once converged), hval_dev = the last H.  stats
+ * (nullable host struct).  Synchronous on return.  Errors: EINVAL (NULL handle, h or sweeps
+ * out of range), ENOMEM, EUNSUPPORTED (an n-bit set does not fit in shared memory). */
+htd_status htd_hindex_decompose(htd_graph *g, int32_t h, int32_t sweeps, int32_t max_iter,
+                                int32_t *truss_dev, int32_t *hval_dev, htd_hindex_stats *stats,
+                                void *stream);
+
 /* ---- Served decomposition: a request loop with continuous batching -------------------
  *
  * The paper decomposes one graph per call; a server decomposes a stream of independent

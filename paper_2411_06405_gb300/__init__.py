@@ -28,7 +28,7 @@ __all__ = [
     "HtdStats",
     "Graph", "htd_build_csr", "htd_graph_info", "htd_edges", "htd_csr", "htd_h_support",
     "htd_truss_decompose", "htd_truss_decompose_host", "htd_h_support_static", "htd_graph_free",
-    "htd_truss_decompose_batched", "Server", "htd_footprint_estimate",
+    "htd_truss_decompose_batched", "Server", "htd_footprint_estimate", "htd_hindex_decompose",
     "library_path",
 ]
 
@@ -237,6 +237,20 @@ def htd_h_support_static(n: int, row_ptr, col, eu, ev, h: int, out, stream=None)
                                                 _ptr(eu), _ptr(ev), int(h), _ptr(out),
                                                 _stream_handle(stream)), "htd_h_support_static")
     return out
+
+
+def htd_hindex_decompose(g: Graph, h: int, sweeps: int = 1, max_iter: int = -1, stream=None):
+    """The H-index iteration of Sec. 4 on the device.  sweeps = 1: synchronous orders
+    (Algorithm 2); sweeps > 1: asynchronous updating by that many edge blocks per order.
+    Returns (truss = H + 2, H, stats dict) as int32 CUDA tensors of m entries."""
+    torch = _torch()
+    t = torch.empty(max(g.m, 1), dtype=torch.int32, device=g.device)
+    hv = torch.empty(max(g.m, 1), dtype=torch.int32, device=g.device)
+    st = _lib.HtdHindexStats()
+    _lib.check(_lib.load().htd_hindex_decompose(g.handle, int(h), int(sweeps), int(max_iter),
+                                                _ptr(t), _ptr(hv), ctypes.byref(st),
+                                                _stream_handle(stream)), "htd_hindex_decompose")
+    return t[:g.m], hv[:g.m], st.as_dict()
 
 
 class Server:

@@ -32,7 +32,7 @@ EXPORTED = (
     "htd_truss_decompose", "htd_truss_decompose_ex", "htd_truss_decompose_host",
     "htd_graph_free", "htd_kernel_launch_count", "htd_status_string", "htd_last_error",
     "htd_h_support_static", "htd_truss_decompose_batched", "htd_batch_plan",
-    "htd_footprint_estimate", "htd_server_create", "htd_server_submit", "htd_server_poll",
+    "htd_hindex_decompose", "htd_footprint_estimate", "htd_server_create", "htd_server_submit", "htd_server_poll",
     "htd_server_wait", "htd_server_info", "htd_server_destroy",
 )
 
@@ -77,6 +77,22 @@ class HtdStats(ctypes.Structure):
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class HtdHindexStats(ctypes.Structure):
+    _fields_ = [
+        ("ball_entries", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
+        ("h", ctypes.c_int32),
+        ("sweeps", ctypes.c_int32),
+        ("iterations", ctypes.c_int32),
+        ("converged", ctypes.c_int32),
+        ("ms_total", ctypes.c_float),
+        ("pad", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
 
 
 class HtdRequestInfo(ctypes.Structure):
@@ -155,6 +171,8 @@ def load():
             "htd_truss_decompose_batched": ([i32, p, p, p, p, p, u32, i32, p, p, p,
                                              ctypes.POINTER(i32), ps, p], ctypes.c_int),
             "htd_batch_plan": ([i32, p, p, p, i32, p, p, ctypes.POINTER(i32)], ctypes.c_int),
+            "htd_hindex_decompose": ([p, i32, i32, i32, p, p, ctypes.POINTER(HtdHindexStats), p],
+                                     ctypes.c_int),
             "htd_footprint_estimate": ([i32, i64, i32, i64], i64),
             "htd_server_create": ([i32, i64, u32, pp], ctypes.c_int),
             "htd_server_submit": ([p, i32, p, p, i64, i32, ctypes.POINTER(i64)], ctypes.c_int),

@@ -139,6 +139,10 @@ htd_status recover_round_h3(Handle *H, cudaStream_t s, int64_t *launches);
 // Initial radius-2 balls of the incremental h = 3 peel (htd_peel.cu).
 htd_status initial_pass_r2(Handle *H, cudaStream_t s, int64_t *launches);
 
+// The H-index iteration of Sec. 4 on the device (htd_hindex.cu); G is H's public handle.
+htd_status hindex_run(htd_graph *G, Handle *H, int32_t h, int32_t sweeps, int32_t max_iter,
+                      int32_t *truss_dev, int32_t *hval_dev, htd_hindex_stats *stats, cudaStream_t s);
+
 // One incremental round (h <= 3) as four (h = 3: five) launches, the graph path (htd_loss.cu).
 htd_status enqueue_incremental_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t *evs,
                                      unsigned record_flags);

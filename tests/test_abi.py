@@ -66,6 +66,7 @@ def test_server_structs_match_header(lib):
 
     assert _struct_fields("htd_request_info") == list(_lib.HtdRequestInfo._fields_)
     assert _struct_fields("htd_server_stats") == list(_lib.HtdServerStats._fields_)
+    assert _struct_fields("htd_hindex_stats") == list(_lib.HtdHindexStats._fields_)
 
 
 def test_footprint_estimate_on_host(lib):
