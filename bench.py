@@ -37,6 +37,8 @@ WORKLOADS = {
 # the other single-GPU workloads reported beside the headline (fewer steps each)
 CONFIG_ENTRIES = ["er_n2000_h2", "dcsbm_n200k_h2", "dcsbm_n200k_h3"]
 CONFIG_STEPS = {"dcsbm_n200k_h3": (1, 0)}  # (timed steps, warm-up steps); default (3, 1)
+# batched form: 4,096 graphs, n ~ U[50, 5000], ER or BA, h ~ U{2,3}
+BATCHED = {"count": 4096, "seed": 0x48545258, "steps": 2, "warmup": 1}
 # served stream: Poisson arrivals at 200 requests/s over R-MAT and BA graphs, h in {2, 3}
 # (the largest pool members are capped so that the stream finishes within the bench run)
 SERVED = {"count": 200, "seed": 0x48545259, "rate": 200.0, "workers": 4,
@@ -400,6 +402,42 @@ def measure_served(htd, count: int, seed: int, rate: float, workers: int, rmat_s
             "retries": int(sum(i["retries"] for i in infos))}
 
 
+def measure_batched(htd, torch, count: int, seed: int, steps: int, warmup: int, stream, flush,
+                    max_union_vertices: int = 0, flags: int = 0):
+    """Batched form: `count` small graphs of mixed h decomposed by one call, inputs resident
+    on the device; graphs generated beforehand (in parallel processes)."""
+    import multiprocessing as mp
+
+    from synth import batch_graphs
+
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        graphs = batch_graphs(count, seed, pool=pool)
+    b = htd.BatchInput(graphs)
+    res, st = None, None
+    for _ in range(warmup):
+        res, st = htd.htd_truss_decompose_batched(b, flags=flags, max_union_vertices=max_union_vertices)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res, st = htd.htd_truss_decompose_batched(b, flags=flags, max_union_vertices=max_union_vertices)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(e))
+    edges = float(sum(int(r.numel()) for r in res))
+    mean = float(np.mean(ms))
+    return {"workload": f"batched_{count}", "graphs": count, "seed": seed,
+            "vertices": int(b.n[:count].sum()), "raw_pairs": b.total, "edges": edges,
+            "h_counts": {str(v): int((b.h[:count] == v).sum()) for v in (2, 3)},
+            "steps": steps, "warmup": warmup, "ms_per_step": mean,
+            "edges_per_sec": edges / (mean / 1e3), "graphs_per_sec": count / (mean / 1e3),
+            "unions": st["unions"], "rounds_sum_over_unions": st["rounds"],
+            "rounds_rebuilt": st["rounds_rebuilt"], "max_union_vertices": max_union_vertices,
+            "flags": flags}
+
+
 def host_np(t):
     return t.cpu().numpy() if t is not None else None
 
@@ -461,6 +499,9 @@ def run_gpu(args, world, rank, local):
         rc, _, _ = measure_workload(htd, torch, lib, cname, ch, st_, wu_, flush, stream, dev,
                                     peaks, profile=True)
         configs[wl] = rc
+    if not args.no_batched:
+        configs["batched_4096"] = measure_batched(htd, torch, BATCHED["count"], BATCHED["seed"],
+                                                  BATCHED["steps"], BATCHED["warmup"], stream, flush)
     if not args.no_served:
         configs["served_poisson"] = measure_served(htd, SERVED["count"], SERVED["seed"],
                                                    SERVED["rate"], SERVED["workers"],
@@ -528,6 +569,7 @@ def main():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other single-GPU workloads' entries")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream entry")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched entry")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if world > 1:

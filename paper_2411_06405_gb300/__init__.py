@@ -28,7 +28,7 @@ __all__ = [
     "HtdStats",
     "Graph", "htd_build_csr", "htd_graph_info", "htd_edges", "htd_csr", "htd_h_support",
     "htd_truss_decompose", "htd_truss_decompose_host", "htd_h_support_static", "htd_graph_free",
-    "htd_truss_decompose_batched", "Server", "htd_footprint_estimate", "htd_hindex_decompose",
+    "htd_truss_decompose_batched", "BatchInput", "Server", "htd_footprint_estimate", "htd_hindex_decompose",
     "library_path",
 ]
 
@@ -188,43 +188,55 @@ def htd_truss_decompose_host(n: int, src, dst, h: int, out_eu=None, out_ev=None,
     return out_eu[:mm], out_ev[:mm], out_truss[:mm], stats.as_dict()
 
 
+class BatchInput:
+    """A batch of graphs concatenated once on the device (raw pairs with per-graph offsets),
+    so that it can be decomposed repeatedly with its inputs resident."""
+
+    def __init__(self, graphs, device=None):
+        torch = _torch()
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        k = len(graphs)
+        self.count = k
+        self.n = np.zeros(max(k, 1), dtype=np.int32)
+        self.h = np.zeros(max(k, 1), dtype=np.int32)
+        self.off = np.zeros(k + 1, dtype=np.int64)
+        srcs, dsts = [], []
+        for i, (ng, s, d, hg) in enumerate(graphs):
+            s = np.ascontiguousarray(s.cpu().numpy() if hasattr(s, "cpu") else s, dtype=np.int32).reshape(-1)
+            d = np.ascontiguousarray(d.cpu().numpy() if hasattr(d, "cpu") else d, dtype=np.int32).reshape(-1)
+            if s.shape != d.shape:
+                raise ValueError(f"graph {i}: src and dst differ in length")
+            self.n[i], self.h[i] = int(ng), int(hg)
+            self.off[i + 1] = self.off[i] + s.size
+            srcs.append(s)
+            dsts.append(d)
+        self.total = int(self.off[-1])
+        cat = lambda xs: np.concatenate(xs) if xs else np.zeros(0, np.int32)
+        self.src = torch.from_numpy(cat(srcs)).to(dev)
+        self.dst = torch.from_numpy(cat(dsts)).to(dev)
+        self.out = torch.empty(max(self.total, 1), dtype=torch.int32, device=dev)
+        self.device = dev
+
+
 def htd_truss_decompose_batched(graphs, flags: int = 0, max_union_vertices: int = 0,
                                 device=None, stream=None):
-    """Decomposes many graphs in one call.  ``graphs``: a sequence of (n, src, dst, h) with
-    src/dst int32 tensors or numpy arrays of local ids in [0, n).  Returns (list of int32
-    CUDA tensors, one per graph, t(e,h) over that graph's canonical edges; stats dict with
-    the number of unions under "unions")."""
-    torch = _torch()
-    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
-    k = len(graphs)
-    n = np.zeros(k, dtype=np.int32)
-    h = np.zeros(k, dtype=np.int32)
-    off = np.zeros(k + 1, dtype=np.int64)
-    srcs, dsts = [], []
-    for i, (ng, s, d, hg) in enumerate(graphs):
-        s = torch.as_tensor(np.asarray(s) if isinstance(s, np.ndarray) else s).to(torch.int32).reshape(-1)
-        d = torch.as_tensor(np.asarray(d) if isinstance(d, np.ndarray) else d).to(torch.int32).reshape(-1)
-        if s.shape != d.shape:
-            raise ValueError(f"graph {i}: src and dst differ in length")
-        n[i], h[i] = int(ng), int(hg)
-        off[i + 1] = off[i] + s.numel()
-        srcs.append(s)
-        dsts.append(d)
-    total = int(off[-1])
-    src = torch.cat(srcs).to(dev) if total else torch.empty(0, dtype=torch.int32, device=dev)
-    dst = torch.cat(dsts).to(dev) if total else torch.empty(0, dtype=torch.int32, device=dev)
-    out = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+    """Decomposes many graphs in one call.  ``graphs``: a BatchInput, or a sequence of
+    (n, src, dst, h) with src/dst int32 tensors or numpy arrays of local ids in [0, n).
+    Returns (list of int32 CUDA tensors, one per graph, t(e,h) over that graph's canonical
+    edges; stats dict with the number of unions under "unions")."""
+    b = graphs if isinstance(graphs, BatchInput) else BatchInput(graphs, device)
+    k = b.count
     out_off = np.zeros(max(k, 1), dtype=np.int64)
     out_m = np.zeros(max(k, 1), dtype=np.int64)
     unions = ctypes.c_int32()
     stats = HtdStats()
     vp = lambda a: ctypes.c_void_p(a.ctypes.data)
     st = _lib.load().htd_truss_decompose_batched(
-        k, vp(n), vp(h), vp(off), _ptr(src), _ptr(dst), int(flags), int(max_union_vertices),
-        ctypes.c_void_p(out.data_ptr()), vp(out_off), vp(out_m), ctypes.byref(unions),
-        ctypes.byref(stats), _stream_handle(stream))
+        k, vp(b.n), vp(b.h), vp(b.off), _ptr(b.src), _ptr(b.dst), int(flags),
+        int(max_union_vertices), ctypes.c_void_p(b.out.data_ptr()), vp(out_off), vp(out_m),
+        ctypes.byref(unions), ctypes.byref(stats), _stream_handle(stream))
     _lib.check(st, "htd_truss_decompose_batched")
-    res = [out[int(out_off[i]):int(out_off[i]) + int(out_m[i])] for i in range(k)]
+    res = [b.out[int(out_off[i]):int(out_off[i]) + int(out_m[i])] for i in range(k)]
     sd = stats.as_dict()
     sd["unions"] = int(unions.value)
     return res, sd

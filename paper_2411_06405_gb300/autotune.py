@@ -1,0 +1,117 @@
+"""Schedule autotuner for the batched decomposition (many small graphs of mixed h).
+
+The batched call packs the graphs of one hop threshold into disjoint unions and peels each
+union once (``htd_truss_decompose_batched``).  Two knobs decide how the device work is laid
+out, and the best setting depends on the graphs:
+
+* ``max_union_vertices`` -- how many vertices a union holds: large unions put more
+  independent work into every round launch (more edges per warp-level work list), small
+  unions let a union stop as soon as its own members are peeled instead of running until
+  the slowest member of a large union is done;
+* ``flags`` -- the round variant: incremental rounds with every ball dense (one load per
+  membership test), incremental rounds with compact balls (h <= 2), or rebuild rounds.
+
+Graphs are grouped by a key of (h, log2 class of n, log2 class of the largest degree).
+``tune`` times every candidate on a sample of each group (CUDA events, after a warm-up) and
+keeps the fastest; the resulting table is JSON, keyed by group.  ``decompose`` runs a batch
+with a table: each group with its own setting, results returned in input order.  The results
+do not depend on the setting (every candidate is an exact decomposition), only the time.
+"""
+
+from __future__ import annotations
+
+import json
+import math
+from collections import defaultdict
+
+import numpy as np
+
+from . import _lib
+
+CANDIDATES = [
+    {"max_union_vertices": 1 << 14, "flags": 0},
+    {"max_union_vertices": 1 << 16, "flags": 0},
+    {"max_union_vertices": 1 << 18, "flags": 0},
+    {"max_union_vertices": 1 << 16, "flags": _lib.HTD_OPT_COMPACT_BALLS},
+    {"max_union_vertices": 1 << 16, "flags": _lib.HTD_OPT_REBUILD},
+]
+DEFAULT = {"max_union_vertices": 1 << 18, "flags": 0}
+
+
+def group_key(n: int, src, dst, h: int) -> str:
+    """(h, n class, largest-degree class) of a raw graph, as a table key."""
+    s = np.asarray(src)
+    d = np.asarray(dst)
+    ok = s != d
+    deg = np.bincount(np.concatenate([s[ok], d[ok]]), minlength=max(int(n), 1)) if ok.any() else np.zeros(1)
+    nc = int(math.log2(max(int(n), 1)))
+    dc = int(math.log2(max(int(deg.max()), 1)))
+    return f"h{int(h)}_n{nc}_d{dc}"
+
+
+def _time_batch(htd, torch, graphs, cand, reps: int = 2) -> float:
+    b = htd.BatchInput(graphs)
+    htd.htd_truss_decompose_batched(b, flags=cand["flags"], max_union_vertices=cand["max_union_vertices"])
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        htd.htd_truss_decompose_batched(b, flags=cand["flags"],
+                                        max_union_vertices=cand["max_union_vertices"])
+        e.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(e))
+    return best
+
+
+def tune(graphs, sample: int = 64, candidates=None, seed: int = 0):
+    """Times the candidates on up to `sample` graphs of every group; returns the table
+    {key: {"max_union_vertices", "flags", "ms": {candidate index: ms}}}."""
+    import torch
+
+    import paper_2411_06405_gb300 as htd
+
+    cands = candidates or CANDIDATES
+    groups = defaultdict(list)
+    for g in graphs:
+        groups[group_key(*g)].append(g)
+    rng = np.random.default_rng(seed)
+    table = {}
+    for key, gs in sorted(groups.items()):
+        pick = gs if len(gs) <= sample else [gs[i] for i in rng.choice(len(gs), sample, replace=False)]
+        times = {}
+        for ci, c in enumerate(cands):
+            times[ci] = _time_batch(htd, torch, pick, c)
+        best = min(times, key=times.get)
+        table[key] = dict(cands[best], ms=times, sample=len(pick))
+    return table
+
+
+def save(table, path: str):
+    with open(path, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+
+
+def load(path: str):
+    with open(path) as f:
+        return json.load(f)
+
+
+def decompose(graphs, table=None, device=None):
+    """Decomposes a batch with the table's setting for each group (DEFAULT for groups the
+    table lacks); returns (list of int32 CUDA tensors in input order, {setting: graphs})."""
+    import paper_2411_06405_gb300 as htd
+
+    table = table or {}
+    parts = defaultdict(list)
+    for i, g in enumerate(graphs):
+        ent = table.get(group_key(*g), DEFAULT)
+        parts[(int(ent["max_union_vertices"]), int(ent["flags"]))].append(i)
+    out = [None] * len(graphs)
+    for (cap, flags), idx in sorted(parts.items()):
+        res, _ = htd.htd_truss_decompose_batched([graphs[i] for i in idx], flags=flags,
+                                                 max_union_vertices=cap, device=device)
+        for i, r in zip(idx, res):
+            out[i] = r
+    return out, {f"{cap}/{flags}": len(idx) for (cap, flags), idx in parts.items()}

@@ -118,6 +118,16 @@ __device__ __forceinline__ void overflow_at(const LossArgs &a, DevStatus *st, in
     else atomicMin(&st->overflow_unit, u);
 }
 
+// Supports of edges 4q .. 4q+3 (e0 = 4q) in one 16-byte load; INT_MAX past m.
+__device__ __forceinline__ int4 load_sup4(const int32_t *sup, int64_t m, int64_t e0) {
+    if (e0 + 3 < m) return *reinterpret_cast<const int4 *>(sup + e0);
+    int4 v = make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
+    if (e0 < m) v.x = sup[e0];
+    if (e0 + 1 < m) v.y = sup[e0 + 1];
+    if (e0 + 2 < m) v.z = sup[e0 + 2];
+    return v;
+}
+
 // Round kernels do nothing once the peel is over or a round halted.
 __device__ __forceinline__ bool round_idle(const LossArgs &a) {
     return vload(a.st->alive) == 0 || vload(a.st->halt) != 0;
@@ -208,6 +218,55 @@ __device__ __forceinline__ T warp_incl_scan(T v) {
         if (lane >= o) v += t;
     }
     return v;
+}
+
+// Hard pairs whose shorter row is long are settled by the whole warp from the two
+// alive-adjacency sets instead of a walk: a common alive neighbour exists iff the AND of
+// the two n-bit sets is non-zero.  A walk of L slots takes L dependent-ish random loads; the
+// AND takes 2W/4 coalesced 16-byte loads, so it wins once L exceeds about W/4.
+__device__ __forceinline__ void warp_dense_pairs(const LossArgs &a, int &state, int p, int q,
+                                                 unsigned &reads) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    bool dense = false;
+    const uint32_t *ps = nullptr, *qs = nullptr;
+    if (state == kHard) {
+        const int len = min(a.row_ptr[p + 1] - a.row_ptr[p], a.row_ptr[q + 1] - a.row_ptr[q]);
+        if (4 * len > a.Wpad) {
+            unsigned r = 0;
+            ps = hub_set(a, p, r);
+            qs = hub_set(a, q, r);
+            reads += r;
+            dense = ps && qs;
+        }
+    }
+    unsigned todo = __ballot_sync(full, dense);
+    while (todo) {
+        const int l = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint4 *p4 = reinterpret_cast<const uint4 *>(
+            __shfl_sync(full, reinterpret_cast<unsigned long long>(ps), l));
+        const uint4 *q4 = reinterpret_cast<const uint4 *>(
+            __shfl_sync(full, reinterpret_cast<unsigned long long>(qs), l));
+        const int nv = a.Wpad >> 2;
+        bool hit = false;
+        for (int i0 = 0; i0 < nv && !hit; i0 += 4 * 32) {
+            uint4 x[4], y[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int i = i0 + 32 * j + lane;
+                x[j] = i < nv ? p4[i] : make_uint4(0, 0, 0, 0);
+                y[j] = i < nv ? q4[i] : make_uint4(0, 0, 0, 0);
+            }
+            unsigned any = 0u;
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                any |= (x[j].x & y[j].x) | (x[j].y & y[j].y) | (x[j].z & y[j].z) | (x[j].w & y[j].w);
+            hit = __any_sync(full, any != 0u);
+            reads += 32;
+        }
+        if (lane == l) state = hit ? kKept : kLost;
+    }
 }
 
 // Common alive neighbours for the warp's hard pairs (lanes with state == kHard; p the
@@ -537,7 +596,10 @@ __device__ void ph_detect(const LossArgs &a) {
             pairs++;
             state = pair_quick(a, p, q, reads);
         }
-        if (__any_sync(0xffffffffu, state == kHard)) warp_hard_pairs(a, state, p, q, reads);
+        if (__any_sync(0xffffffffu, state == kHard)) {
+            warp_dense_pairs(a, state, p, q, reads);
+            if (__any_sync(0xffffffffu, state == kHard)) warp_hard_pairs(a, state, p, q, reads);
+        }
         record_lost_warp(a, st, state == kLost, r.x, z, u, reads);
         reads_total += reads;
     }
@@ -958,19 +1020,23 @@ __device__ void ph_select_items(const LossArgs &a) {
     }
     const int k = vload(st->k), round = vload(st->round), thr = k - 2;
     const int lane = threadIdx.x & 31;
-    const int64_t stride = 4 * (int64_t)gridDim.x * blockDim.x;
-    // four coalesced loads per thread per step, issued before any of them is used
-    for (int64_t e0 = 4 * (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)); e0 < a.m;
+    const int64_t stride = 16 * (int64_t)gridDim.x * blockDim.x;
+    // four 16-byte loads per thread per step (16 supports), issued before any is used
+    for (int64_t e0 = 16 * (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)); e0 < a.m;
          e0 += stride) {
-        int sv[4];
+        int sv[16];
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const int64_t e = e0 + 32 * j + lane;
-            sv[j] = (e < a.m) ? a.sup[e] : INT_MAX;
+            const int4 v = load_sup4(a.sup, a.m, e0 + 4 * (32 * j + lane));
+            sv[4 * j] = v.x;
+            sv[4 * j + 1] = v.y;
+            sv[4 * j + 2] = v.z;
+            sv[4 * j + 3] = v.w;
         }
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int e = (int)(e0 + 32 * j + lane);
+        for (int jj = 0; jj < 16; jj++) {
+            const int j = jj;
+            const int e = (int)(e0 + 4 * (32 * (jj >> 2) + lane) + (jj & 3));
             const bool p = sv[j] <= thr;
             const unsigned bal = __ballot_sync(0xffffffffu, p);
             if (bal == 0u) continue;

@@ -93,20 +93,31 @@ __device__ __forceinline__ void minreduce_body(const int32_t *__restrict__ sup, 
     __shared__ bool s_last;
     int lmin = INT_MAX;
     long long lc = 0;
-    // four coalesced loads per thread per step, issued before any of them is used
-    const int64_t stride = 4 * (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e0 = 4 * (blockIdx.x * (int64_t)blockDim.x) + threadIdx.x; e0 < m; e0 += stride) {
-        int sv[4];
+    // four 16-byte loads per thread per step (16 supports), issued before any is used
+    const int64_t stride = 16 * (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = 16 * (blockIdx.x * (int64_t)blockDim.x) + 4 * threadIdx.x; e0 < m; e0 += stride) {
+        int4 v[4];
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const int64_t e = e0 + (int64_t)j * blockDim.x;
-            sv[j] = (e < m) ? sup[e] : INT_MAX;
+            const int64_t e = e0 + 4 * (int64_t)j * blockDim.x;
+            if (e + 3 < m) {
+                v[j] = *reinterpret_cast<const int4 *>(sup + e);
+            } else {
+                v[j] = make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
+                if (e < m) v[j].x = sup[e];
+                if (e + 1 < m) v[j].y = sup[e + 1];
+                if (e + 2 < m) v[j].z = sup[e + 2];
+            }
         }
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            if (sv[j] != INT_MAX) {
-                lmin = min(lmin, sv[j]);
-                lc++;
+            const int sv[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                if (sv[c] != INT_MAX) {
+                    lmin = min(lmin, sv[c]);
+                    lc++;
+                }
             }
         }
     }

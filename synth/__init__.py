@@ -10,7 +10,9 @@ from .generators import (  # noqa: F401
     CONFIG_SEED_BASE,
     GraphSpec,
     barabasi_albert,
+    batch_graph,
     batch_graphs,
+    batch_params,
     config_graph,
     dcsbm,
     erdos_renyi_gnm,

@@ -252,11 +252,9 @@ def config_graph(name: str) -> GraphSpec:
     raise KeyError(name)
 
 
-def batch_graphs(count: int, seed: int, n_lo: int = 50, n_hi: int = 5000):
-    """A batch of small graphs: per graph n ~ U[n_lo, n_hi], either Erdos-Renyi with mean
-    degree 8 (M = 4n distinct pairs) or Barabasi-Albert with m0 ~ U{2..8}, and a hop
-    threshold h ~ U{2,3}.  Graph i draws its edges from sub-seed seed ^ i.  Returns a list
-    of (n, src, dst, h)."""
+def batch_params(count: int, seed: int, n_lo: int = 50, n_hi: int = 5000):
+    """Per-graph parameters of a batch, drawn in order from one seeded stream: a list of
+    (sub_seed, n, h, kind, m0) with kind 0 = Erdos-Renyi (mean degree 8), 1 = BA."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
@@ -264,14 +262,32 @@ def batch_graphs(count: int, seed: int, n_lo: int = 50, n_hi: int = 5000):
         n = int(rng.integers(n_lo, n_hi + 1))
         h = int(rng.integers(2, 4))
         if rng.random() < 0.5:
-            m = min(4 * n, n * (n - 1) // 2)
-            s, d = erdos_renyi_gnm(n, m, sub)
+            out.append((sub, n, h, 0, 0))
         else:
             m0 = int(rng.integers(2, 9))
-            n = max(n, m0 + 1)
-            s, d = barabasi_albert(n, m0, sub)
-        out.append((n, s, d, h))
+            out.append((sub, max(n, m0 + 1), h, 1, m0))
     return out
+
+
+def batch_graph(param):
+    """One graph of a batch from its batch_params entry: (n, src, dst, h)."""
+    sub, n, h, kind, m0 = param
+    if kind == 0:
+        s, d = erdos_renyi_gnm(n, min(4 * n, n * (n - 1) // 2), sub)
+    else:
+        s, d = barabasi_albert(n, m0, sub)
+    return n, s, d, h
+
+
+def batch_graphs(count: int, seed: int, n_lo: int = 50, n_hi: int = 5000, pool=None):
+    """A batch of small graphs: per graph n ~ U[n_lo, n_hi], either Erdos-Renyi with mean
+    degree 8 (M = 4n distinct pairs) or Barabasi-Albert with m0 ~ U{2..8}, and a hop
+    threshold h ~ U{2,3}.  Graph i draws its edges from sub-seed seed ^ i.  Returns a list
+    of (n, src, dst, h).  `pool` (optional): a process pool whose map builds the graphs."""
+    params = batch_params(count, seed, n_lo, n_hi)
+    if pool is not None:
+        return list(pool.map(batch_graph, params, chunksize=16))
+    return [batch_graph(p) for p in params]
 
 
 def served_requests(count: int, seed: int, rate: float = 200.0, rmat_scales=(10, 20),

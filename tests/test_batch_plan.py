@@ -66,3 +66,14 @@ def test_plan_rejects_what_the_batched_call_rejects(lib):
     assert plan(lib, [2_000_000], [2], [0], 0)[0] == 6
     assert plan(lib, [4], [2], [1 << 31], 0)[0] == 5
     assert lib.htd_batch_plan(0, None, None, None, 0, None, None, None) == 0
+
+
+def test_autotune_group_keys():
+    from paper_2411_06405_gb300 import autotune
+
+    s = np.array([0, 0, 0, 1], np.int32)
+    d = np.array([1, 2, 3, 2], np.int32)
+    assert autotune.group_key(4, s, d, 2) == "h2_n2_d1"   # n = 4, largest degree 3
+    assert autotune.group_key(1000, s, d, 3).startswith("h3_n9_")
+    # loops do not count towards degrees; an edgeless graph has class 0
+    assert autotune.group_key(5, np.array([1, 1]), np.array([1, 1]), 2) == "h2_n2_d0"

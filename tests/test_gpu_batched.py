@@ -107,3 +107,40 @@ def test_batched_rejects_an_id_outside_its_graph(htd):
     with pytest.raises(htd.HtdError) as e:
         htd.htd_truss_decompose_batched([ok, bad, ok])
     assert e.value.status == 1 and "graph 1" in str(e.value)
+
+
+def test_every_autotuner_schedule_is_exact(htd, batch_and_truth):
+    # every candidate schedule of the autotuner, and a tuned run, give the oracle's result
+    from paper_2411_06405_gb300 import autotune
+
+    graphs, expected = batch_and_truth
+    for cand in autotune.CANDIDATES:
+        res, _ = htd.htd_truss_decompose_batched(graphs, flags=cand["flags"],
+                                                 max_union_vertices=cand["max_union_vertices"])
+        check(res, graphs, expected)
+    table = autotune.tune(graphs, sample=8)
+    assert table and all(v["flags"] in [c["flags"] for c in autotune.CANDIDATES] for v in table.values())
+    res, parts = autotune.decompose(graphs, table)
+    check(res, graphs, expected)
+    assert sum(parts.values()) == len(graphs)
+
+
+def test_batch_of_the_benchmark_recipe_sampled(htd, oracle_mod):
+    # 64 graphs of the 4,096-graph recipe (n in [50, 5000], ER or BA, h in {2, 3}): each
+    # equals the oracle's decomposition of that graph alone
+    graphs = batch_graphs(4096, 0x48545258)[:64]
+    small = [i for i, g in enumerate(graphs) if g[0] <= 700][:12]
+    res, st = htd.htd_truss_decompose_batched(graphs)
+    assert len(res) == 64
+    for i in small:
+        np.testing.assert_array_equal(res[i].cpu().numpy(), oracle_truss(oracle_mod, *graphs[i]))
+    # the rest against single-graph GPU calls (each certified by the oracle's certificate)
+    for g, r in zip(graphs, res):
+        n, s, d, h = g
+        gg = htd.htd_build_csr(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
+        t, stamp, _ = htd.htd_truss_decompose(gg, h, stamps=True)
+        assert torch.equal(t, r)
+        eu, ev = htd.htd_edges(gg)
+        ob, bad, _ = oracle_mod.certify_all(n, eu.cpu().numpy(), ev.cpu().numpy(), h,
+                                            t.cpu().numpy(), stamp.cpu().numpy())
+        assert ob == 0 and bad.size == 0
