@@ -500,8 +500,14 @@ def run_gpu(args, world, rank, local):
                                     peaks, profile=True)
         configs[wl] = rc
     if not args.no_batched:
+        # the same batch under the two schedules: unions peeled round by round, and one
+        # block per graph with all rounds inside one persistent launch
         configs["batched_4096"] = measure_batched(htd, torch, BATCHED["count"], BATCHED["seed"],
-                                                  BATCHED["steps"], BATCHED["warmup"], stream, flush)
+                                                  BATCHED["steps"], BATCHED["warmup"], stream, flush,
+                                                  flags=htd.HTD_OPT_BATCH_BLOCKS)
+        configs["batched_4096_unions"] = measure_batched(htd, torch, BATCHED["count"],
+                                                         BATCHED["seed"], BATCHED["steps"],
+                                                         BATCHED["warmup"], stream, flush)
     if not args.no_served:
         configs["served_poisson"] = measure_served(htd, SERVED["count"], SERVED["seed"],
                                                    SERVED["rate"], SERVED["workers"],

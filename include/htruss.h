@@ -125,6 +125,13 @@ typedef struct htd_stats {
                                        free memory); with this flag, or when they do not
                                        fit, h = 3 peels by rebuilds */
 
+#define HTD_OPT_BATCH_BLOCKS 64u    /* htd_truss_decompose_batched: every graph of at most
+                                       8,192 vertices and h <= 3 is peeled by one block of a
+                                       single persistent launch, all of its rounds inside the
+                                       kernel (radius-1..h balls as bit rows, candidates'
+                                       balls recomputed by ORs); larger graphs take the union
+                                       path (same results) */
+
 /* Normalise an undirected edge list and build the graph (Sec. 2 graph model).
  *   n            vertex count, ids in [0, n); 0 <= n <= HTD_MAX_N.
  *   src, dst     m_in int32 endpoints each (device pointers if inputs_on_device != 0,

@@ -20,11 +20,12 @@ import numpy as np
 from . import _lib
 from ._lib import (HTD_MAX_H, HTD_MAX_N, HTD_OPT_NO_GRAPH, HTD_OPT_REBUILD, HTD_OPT_TIMING,
                    HTD_OPT_TINY_LOSS_TABLE, HTD_OPT_PERSISTENT_ROUNDS, HTD_OPT_COMPACT_BALLS,
-                   HtdError, HtdStats)
+                   HTD_OPT_BATCH_BLOCKS, HtdError, HtdStats)
 
 __all__ = [
     "HTD_MAX_H", "HTD_MAX_N", "HTD_OPT_NO_GRAPH", "HTD_OPT_REBUILD", "HTD_OPT_TIMING",
-    "HTD_OPT_TINY_LOSS_TABLE", "HTD_OPT_PERSISTENT_ROUNDS", "HTD_OPT_COMPACT_BALLS", "HtdError",
+    "HTD_OPT_TINY_LOSS_TABLE", "HTD_OPT_PERSISTENT_ROUNDS", "HTD_OPT_COMPACT_BALLS",
+    "HTD_OPT_BATCH_BLOCKS", "HtdError",
     "HtdStats",
     "Graph", "htd_build_csr", "htd_graph_info", "htd_edges", "htd_csr", "htd_h_support",
     "htd_truss_decompose", "htd_truss_decompose_host", "htd_h_support_static", "htd_graph_free",

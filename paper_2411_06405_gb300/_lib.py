@@ -25,6 +25,7 @@ HTD_OPT_REBUILD = 4
 HTD_OPT_TINY_LOSS_TABLE = 8
 HTD_OPT_PERSISTENT_ROUNDS = 16
 HTD_OPT_COMPACT_BALLS = 32
+HTD_OPT_BATCH_BLOCKS = 64
 
 # every symbol include/htruss.h declares
 EXPORTED = (

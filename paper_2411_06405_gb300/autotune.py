@@ -8,8 +8,9 @@ out, and the best setting depends on the graphs:
   independent work into every round launch (more edges per warp-level work list), small
   unions let a union stop as soon as its own members are peeled instead of running until
   the slowest member of a large union is done;
-* ``flags`` -- the round variant: incremental rounds with every ball dense (one load per
-  membership test), incremental rounds with compact balls (h <= 2), or rebuild rounds.
+* ``flags`` -- the schedule: one block per graph with every round inside one persistent
+  launch (``HTD_OPT_BATCH_BLOCKS``), or union peels with incremental rounds on dense balls
+  (one load per membership test), on compact balls (h <= 2), or rebuild rounds.
 
 Graphs are grouped by a key of (h, log2 class of n, log2 class of the largest degree).
 ``tune`` times every candidate on a sample of each group (CUDA events, after a warm-up) and
@@ -29,6 +30,7 @@ import numpy as np
 from . import _lib
 
 CANDIDATES = [
+    {"max_union_vertices": 1 << 18, "flags": _lib.HTD_OPT_BATCH_BLOCKS},
     {"max_union_vertices": 1 << 14, "flags": 0},
     {"max_union_vertices": 1 << 16, "flags": 0},
     {"max_union_vertices": 1 << 18, "flags": 0},
@@ -115,3 +117,34 @@ def decompose(graphs, table=None, device=None):
         for i, r in zip(idx, res):
             out[i] = r
     return out, {f"{cap}/{flags}": len(idx) for (cap, flags), idx in parts.items()}
+
+
+TABLE_PATH = __import__("os").path.join(__import__("os").path.dirname(__file__), "tuning",
+                                        "batched_gb300.json")
+
+
+def main(argv=None):
+    """Tunes the schedules on a sample of the 4,096-graph batch recipe and writes the table."""
+    import argparse
+    import os
+
+    import torch
+
+    from synth import batch_graphs
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=TABLE_PATH)
+    ap.add_argument("--graphs", type=int, default=1024)
+    ap.add_argument("--sample", type=int, default=48)
+    args = ap.parse_args(argv)
+    torch.cuda.set_device(0)
+    graphs = batch_graphs(4096, 0x48545258)[: args.graphs]
+    table = tune(graphs, sample=args.sample)
+    os.makedirs(os.path.dirname(args.out), exist_ok=True)
+    save(table, args.out)
+    print(json.dumps({k: {"max_union_vertices": v["max_union_vertices"], "flags": v["flags"]}
+                      for k, v in table.items()}))
+
+
+if __name__ == "__main__":
+    main()

@@ -24,6 +24,7 @@ constexpr int kRoundsPerGraph = 16;
 }  // namespace
 
 void set_last_error(const std::string &msg) { g_last_error = msg; }
+GraphDev *graph_dev(htd_graph *g) { return &g->H.g; }
 void add_launches(int64_t k) { g_launches += k; }
 
 }  // namespace htd

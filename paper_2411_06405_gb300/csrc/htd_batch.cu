@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "htd_internal.h"
@@ -108,7 +109,7 @@ struct UnionPlan {
 // graph larger than cap_n forms a union alone).
 htd_status plan_unions(const char *who, int32_t num_graphs, const int32_t *n, const int32_t *h,
                        const int64_t *edge_offsets, int32_t max_union_vertices,
-                       std::vector<UnionPlan> *plan) {
+                       std::vector<UnionPlan> *plan, const std::vector<char> *include = nullptr) {
     if (num_graphs < 0 || (num_graphs > 0 && (!n || !h || !edge_offsets))) {
         set_last_error(std::string(who) + ": NULL argument or num_graphs < 0");
         return HTD_EINVAL;
@@ -137,7 +138,7 @@ htd_status plan_unions(const char *who, int32_t num_graphs, const int32_t *n, co
     plan->clear();
     for (int32_t hh = 1; hh <= HTD_MAX_H; hh++) {
         for (int32_t g = 0; g < num_graphs; g++) {
-            if (h[g] != hh) continue;
+            if (h[g] != hh || (include && !(*include)[g])) continue;
             const int64_t cnt = edge_offsets[g + 1] - edge_offsets[g];
             if (plan->empty() || plan->back().h != hh || plan->back().n + n[g] > cap_n ||
                 plan->back().pairs + cnt > kMaxUnionPairs) {
@@ -168,6 +169,79 @@ struct UnionScratch {
     }
 };
 
+// Gathers a union's pairs (ids shifted), builds its graph on U->g and finds each member's
+// range [b[j], t[j]) of the union's canonical edges (the edges whose smaller endpoint lies
+// in the member's id range).  *mu receives the union's edge count.  A union without any
+// pair builds nothing (mu = 0, empty ranges).
+htd_status build_union(const UnionPlan &up, const int32_t *src_dev, const int32_t *dst_dev,
+                       void *stream, UnionScratch *U, int64_t *mu_out, std::vector<int64_t> *b,
+                       std::vector<int64_t> *t, bool unused = false) {
+    (void)unused;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const std::vector<Member> &mem = up.mem;
+    const std::vector<int32_t> &ids = up.ids;
+    const int64_t nu = up.n, pairs = up.pairs;
+    b->assign(mem.size(), 0);
+    t->assign(mem.size(), 0);
+    *mu_out = 0;
+    if (pairs == 0) return HTD_OK;
+    cudaError_t e = cudaMalloc(&U->mem, mem.size() * sizeof(Member));
+    if (e == cudaSuccess) e = cudaMalloc(&U->usrc, pairs * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&U->udst, pairs * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&U->bad, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(U->mem, mem.data(), mem.size() * sizeof(Member), cudaMemcpyHostToDevice, s);
+    const int none = INT32_MAX;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(U->bad, &none, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const int64_t blocks = std::min<int64_t>((pairs + kBlock - 1) / kBlock, 4096);
+        k_union_gather<<<(unsigned)blocks, kBlock, 0, s>>>(U->mem, (int)mem.size(), pairs, src_dev, dst_dev,
+                                                          U->usrc, U->udst, U->bad);
+        add_launches(1);
+        e = cudaGetLastError();
+    }
+    int bad = INT32_MAX;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, U->bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_last_error(std::string("htd_truss_decompose_batched: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? HTD_ENOMEM : HTD_ECUDA;
+    }
+    if (bad != INT32_MAX) {
+        set_last_error("htd_truss_decompose_batched: graph " + std::to_string(ids[bad]) +
+                       ": an endpoint outside [0, n)");
+        return HTD_EINVAL;
+    }
+    htd_status st = htd_build_csr((int32_t)nu, U->usrc, U->udst, pairs, 1, stream, &U->g);
+    if (st != HTD_OK) return st;
+    int32_t nn = 0;
+    int64_t mu = 0;
+    htd_graph_info(U->g, &nn, &mu);
+    std::vector<int32_t> eu(mu > 0 ? mu : 1);
+    if (mu > 0) {
+        e = cudaMemcpyAsync(eu.data(), graph_dev(U->g)->eu, mu * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_last_error(std::string("htd_truss_decompose_batched: ") + cudaGetErrorString(e));
+            return HTD_ECUDA;
+        }
+    }
+    for (size_t j = 0; j < mem.size(); j++) {
+        const int32_t lo_id = mem[j].voff, hi_id = mem[j].voff + mem[j].n;
+        (*b)[j] = std::lower_bound(eu.begin(), eu.begin() + mu, lo_id) - eu.begin();
+        (*t)[j] = std::lower_bound(eu.begin(), eu.begin() + mu, hi_id) - eu.begin();
+    }
+    *mu_out = mu;
+    return HTD_OK;
+}
+
+int num_sms_of_current() {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return nsm > 0 ? nsm : 1;
+}
+
 }  // namespace
 }  // namespace htd
 
@@ -196,91 +270,73 @@ extern "C" htd_status htd_truss_decompose_batched(
     int32_t unions = 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int64_t out_pos = 0;
+    // block mode: graphs of at most kBlockMaxN vertices and h <= 3 are peeled one per block
+    const bool blocks = (flags & HTD_OPT_BATCH_BLOCKS) != 0;
+    std::vector<char> small(num_graphs > 0 ? num_graphs : 1, 0), large(num_graphs > 0 ? num_graphs : 1, 1);
+    if (blocks) {
+        for (int32_t g = 0; g < num_graphs; g++) {
+            small[g] = (n[g] <= kBlockMaxN && h[g] <= 3) ? 1 : 0;
+            large[g] = !small[g];
+        }
+        std::vector<UnionPlan> bplan;
+        const htd_status ps2 = plan_unions("htd_truss_decompose_batched", num_graphs, n, h, edge_offsets,
+                                           max_union_vertices, &bplan, &small);
+        if (ps2 != HTD_OK) return ps2;
+        std::vector<std::unique_ptr<UnionScratch>> held;
+        std::vector<BlockGraphDescHost> descs;
+        for (const UnionPlan &up : bplan) {
+            auto U = std::make_unique<UnionScratch>();
+            std::vector<int64_t> b, t;
+            int64_t mu = 0;
+            const htd_status us = build_union(up, src_dev, dst_dev, stream, U.get(), &mu, &b, &t);
+            if (us != HTD_OK) return us;
+            GraphDev *gdv = U->g ? graph_dev(U->g) : nullptr;
+            for (size_t j = 0; j < up.mem.size(); j++) {
+                out_offsets[up.ids[j]] = out_pos + b[j];
+                out_m[up.ids[j]] = t[j] - b[j];
+                if (t[j] > b[j])
+                    descs.push_back(BlockGraphDescHost{gdv->row_ptr, gdv->col, gdv->slot_eid, gdv->eu, gdv->ev,
+                                                       truss_dev + out_pos + b[j], b[j], t[j] - b[j],
+                                                       up.mem[j].voff, up.mem[j].n, up.h});
+            }
+            out_pos += mu;
+            if (mu > 0) unions++;
+            held.push_back(std::move(U));
+        }
+        int64_t rounds = 0;
+        const htd_status bs = batch_block_run(descs, s, num_sms_of_current(), &rounds);
+        if (bs != HTD_OK) return bs;
+        acc.rounds += rounds;
+        acc.frontier_edges += 0;
+    }
 
-    for (const UnionPlan &up : plan) {
-        const int32_t hh = up.h;
-        const std::vector<Member> &mem = up.mem;
-        const std::vector<int32_t> &ids = up.ids;
-        const int64_t nu = up.n, pairs = up.pairs;
-        if (pairs == 0) {  // no pairs at all: every member has zero edges
-            for (size_t j = 0; j < mem.size(); j++) {
-                out_offsets[ids[j]] = out_pos;
-                out_m[ids[j]] = 0;
-            }
-            continue;
-        }
+    std::vector<UnionPlan> lplan;
+    if (blocks) {
+        const htd_status ps3 = plan_unions("htd_truss_decompose_batched", num_graphs, n, h, edge_offsets,
+                                           max_union_vertices, &lplan, &large);
+        if (ps3 != HTD_OK) return ps3;
+    }
+    for (const UnionPlan &up : (blocks ? lplan : plan)) {
         UnionScratch U;
-        cudaError_t e = cudaSuccess;
-        {
-            e = cudaMalloc(&U.mem, mem.size() * sizeof(Member));
-            if (e == cudaSuccess) e = cudaMalloc(&U.usrc, pairs * sizeof(int32_t));
-            if (e == cudaSuccess) e = cudaMalloc(&U.udst, pairs * sizeof(int32_t));
-            if (e == cudaSuccess) e = cudaMalloc(&U.bad, sizeof(int));
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(U.mem, mem.data(), mem.size() * sizeof(Member),
-                                    cudaMemcpyHostToDevice, s);
-            const int none = INT32_MAX;
-            if (e == cudaSuccess) e = cudaMemcpyAsync(U.bad, &none, sizeof(int), cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) {
-                const int64_t blocks = std::min<int64_t>((pairs + kBlock - 1) / kBlock, 4096);
-                k_union_gather<<<(unsigned)blocks, kBlock, 0, s>>>(U.mem, (int)mem.size(), pairs, src_dev,
-                                                                  dst_dev, U.usrc, U.udst, U.bad);
-                add_launches(1);
-                e = cudaGetLastError();
-            }
-            int bad = INT32_MAX;
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, U.bad, sizeof(int), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) {
-                set_last_error(std::string("htd_truss_decompose_batched: ") + cudaGetErrorString(e));
-                return e == cudaErrorMemoryAllocation ? HTD_ENOMEM : HTD_ECUDA;
-            }
-            if (bad != INT32_MAX) {
-                set_last_error("htd_truss_decompose_batched: graph " + std::to_string(ids[bad]) +
-                               ": an endpoint outside [0, n)");
-                return HTD_EINVAL;
-            }
-        }
-        htd_status st = htd_build_csr((int32_t)nu, U.usrc, U.udst, pairs, 1, stream, &U.g);
-        if (st != HTD_OK) return st;
-        int32_t nn = 0;
+        std::vector<int64_t> b, t;
         int64_t mu = 0;
-        htd_graph_info(U.g, &nn, &mu);
-        htd_stats us;
-        std::memset(&us, 0, sizeof(us));
-        st = htd_truss_decompose_ex(U.g, hh, flags, truss_dev + out_pos, nullptr, &us, stream);
+        htd_status st = build_union(up, src_dev, dst_dev, stream, &U, &mu, &b, &t, true);
         if (st != HTD_OK) return st;
-        add_stats(&acc, us);
-        if (!us.incremental) acc.incremental = 0;
-        // member g's edges: the canonical edges whose smaller endpoint lies in its id range
-        std::vector<int32_t> eu(mu > 0 ? mu : 1);
         if (mu > 0) {
-            int32_t *eu_dev = nullptr, *ev_dev = nullptr;
-            e = cudaMalloc(&eu_dev, mu * sizeof(int32_t));
-            if (e == cudaSuccess) e = cudaMalloc(&ev_dev, mu * sizeof(int32_t));
-            if (e == cudaSuccess) {
-                st = htd_edges(U.g, eu_dev, ev_dev, stream);
-                if (st == HTD_OK)
-                    e = cudaMemcpyAsync(eu.data(), eu_dev, mu * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-                if (st == HTD_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
-            }
-            cudaFree(eu_dev);
-            cudaFree(ev_dev);
+            htd_stats us;
+            std::memset(&us, 0, sizeof(us));
+            st = htd_truss_decompose_ex(U.g, up.h, flags & ~HTD_OPT_BATCH_BLOCKS, truss_dev + out_pos,
+                                        nullptr, &us, stream);
             if (st != HTD_OK) return st;
-            if (e != cudaSuccess) {
-                set_last_error(std::string("htd_truss_decompose_batched: ") + cudaGetErrorString(e));
-                return e == cudaErrorMemoryAllocation ? HTD_ENOMEM : HTD_ECUDA;
-            }
+            add_stats(&acc, us);
+            if (!us.incremental) acc.incremental = 0;
+            unions++;
         }
-        for (size_t j = 0; j < mem.size(); j++) {
-            const int32_t lo_id = mem[j].voff, hi_id = mem[j].voff + mem[j].n;
-            const int64_t b = std::lower_bound(eu.begin(), eu.begin() + mu, lo_id) - eu.begin();
-            const int64_t t = std::lower_bound(eu.begin(), eu.begin() + mu, hi_id) - eu.begin();
-            out_offsets[ids[j]] = out_pos + b;
-            out_m[ids[j]] = t - b;
+        for (size_t j = 0; j < up.mem.size(); j++) {
+            out_offsets[up.ids[j]] = out_pos + b[j];
+            out_m[up.ids[j]] = t[j] - b[j];
         }
         out_pos += mu;
-        unions++;
     }
     if (num_unions) *num_unions = unions;
     if (stats) *stats = acc;

@@ -139,6 +139,22 @@ htd_status recover_round_h3(Handle *H, cudaStream_t s, int64_t *launches);
 // Initial radius-2 balls of the incremental h = 3 peel (htd_peel.cu).
 htd_status initial_pass_r2(Handle *H, cudaStream_t s, int64_t *launches);
 
+// The normalised graph behind a public handle (htd_api.cu).
+GraphDev *graph_dev(htd_graph *g);
+
+// One small graph of a batch for the block-per-graph launch (htd_batch_block.cu): device
+// pointers into its union's CSR, its vertices [v0, v0 + L) and edges [e0, e0 + m) there,
+// and where its t(e,h) go.
+struct BlockGraphDescHost {
+    const int32_t *row_ptr, *col, *slot_eid, *eu, *ev;
+    int32_t *out;
+    int64_t e0, m;
+    int32_t v0, L, h;
+};
+constexpr int32_t kBlockMaxN = 8192;  // largest graph a block peels alone
+htd_status batch_block_run(const std::vector<BlockGraphDescHost> &graphs, cudaStream_t s,
+                           int num_sms, int64_t *rounds_out);
+
 // The H-index iteration of Sec. 4 on the device (htd_hindex.cu); G is H's public handle.
 htd_status hindex_run(htd_graph *G, Handle *H, int32_t h, int32_t sweeps, int32_t max_iter,
                       int32_t *truss_dev, int32_t *hval_dev, htd_hindex_stats *stats, cudaStream_t s);
