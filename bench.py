@@ -402,40 +402,83 @@ def measure_served(htd, count: int, seed: int, rate: float, workers: int, rmat_s
             "retries": int(sum(i["retries"] for i in infos))}
 
 
+_BATCH_CACHE = {}
+
+
+def batch_workload(count: int, seed: int):
+    """The batch's graphs, generated once per run in parallel processes."""
+    if (count, seed) not in _BATCH_CACHE:
+        import multiprocessing as mp
+
+        from synth import batch_graphs
+
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            _BATCH_CACHE[(count, seed)] = batch_graphs(count, seed, pool=pool)
+    return _BATCH_CACHE[(count, seed)]
+
+
 def measure_batched(htd, torch, count: int, seed: int, steps: int, warmup: int, stream, flush,
-                    max_union_vertices: int = 0, flags: int = 0):
-    """Batched form: `count` small graphs of mixed h decomposed by one call, inputs resident
-    on the device; graphs generated beforehand (in parallel processes)."""
-    import multiprocessing as mp
+                    max_union_vertices: int = 0, flags: int = 0, table=None):
+    """Batched form: `count` small graphs of mixed h decomposed by one call (or, with an
+    autotuner table, one call per tuned setting), inputs resident on the device."""
+    from paper_2411_06405_gb300 import autotune
 
-    from synth import batch_graphs
+    graphs = batch_workload(count, seed)
+    if table is not None:
+        prepared = autotune.prepare(graphs, table)
+        run = lambda: autotune.run_prepared(prepared, count)
+        sched = {"schedule": "autotuned", "settings": {f"{c}/{f}": len(i) for _, i, c, f in prepared}}
+    else:
+        b = htd.BatchInput(graphs)
 
-    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        graphs = batch_graphs(count, seed, pool=pool)
-    b = htd.BatchInput(graphs)
+        def run():
+            res, st = htd.htd_truss_decompose_batched(b, flags=flags,
+                                                      max_union_vertices=max_union_vertices)
+            return res, st
+        sched = {"schedule": "blocks" if flags & htd.HTD_OPT_BATCH_BLOCKS else "unions",
+                 "max_union_vertices": max_union_vertices, "flags": flags}
     res, st = None, None
     for _ in range(warmup):
-        res, st = htd.htd_truss_decompose_batched(b, flags=flags, max_union_vertices=max_union_vertices)
+        res, st = run()
     torch.cuda.synchronize()
     ms = []
     for _ in range(steps):
         flush.zero_()
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        res, st = htd.htd_truss_decompose_batched(b, flags=flags, max_union_vertices=max_union_vertices)
+        res, st = run()
         e.record(stream)
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(e))
     edges = float(sum(int(r.numel()) for r in res))
     mean = float(np.mean(ms))
-    return {"workload": f"batched_{count}", "graphs": count, "seed": seed,
-            "vertices": int(b.n[:count].sum()), "raw_pairs": b.total, "edges": edges,
-            "h_counts": {str(v): int((b.h[:count] == v).sum()) for v in (2, 3)},
-            "steps": steps, "warmup": warmup, "ms_per_step": mean,
-            "edges_per_sec": edges / (mean / 1e3), "graphs_per_sec": count / (mean / 1e3),
-            "unions": st["unions"], "rounds_sum_over_unions": st["rounds"],
-            "rounds_rebuilt": st["rounds_rebuilt"], "max_union_vertices": max_union_vertices,
-            "flags": flags}
+    hs = np.array([g[3] for g in graphs])
+    return dict({"workload": f"batched_{count}", "graphs": count, "seed": seed,
+                 "vertices": int(sum(g[0] for g in graphs)),
+                 "raw_pairs": int(sum(g[1].size for g in graphs)), "edges": edges,
+                 "h_counts": {str(v): int((hs == v).sum()) for v in (2, 3)},
+                 "steps": steps, "warmup": warmup, "ms_per_step": mean,
+                 "edges_per_sec": edges / (mean / 1e3), "graphs_per_sec": count / (mean / 1e3),
+                 "unions": st["unions"], "rounds_sum": st["rounds"],
+                 "rounds_rebuilt": st["rounds_rebuilt"]}, **sched)
+
+
+def measure_hindex(htd, torch, name: str, h: int, sweeps_list=(1, 8)):
+    """The paper's H-index iteration (Sec. 4) on a workload: orders to the fixed point and
+    device time, synchronous (Algorithm 2) and with asynchronous updating by edge blocks;
+    the fixed point + 2 is checked against the peel of the same graph."""
+    spec = config_graph(name)
+    g = htd.htd_build_csr(spec.n, torch.from_numpy(spec.src).cuda(), torch.from_numpy(spec.dst).cuda())
+    t_peel, _, _ = htd.htd_truss_decompose(g, h)
+    out = {"workload": f"{name}_h{h}_hindex", "m": g.m}
+    for sw in sweeps_list:
+        t, _, st = htd.htd_hindex_decompose(g, h, sweeps=sw)
+        out[f"sweeps_{sw}"] = {"orders": st["iterations"], "converged": st["converged"],
+                               "ms": st["ms_total"], "edges_per_sec": g.m / (st["ms_total"] / 1e3),
+                               "ball_entries": st["ball_entries"],
+                               "equals_peel": bool(torch.equal(t, t_peel))}
+    g.free()
+    return out
 
 
 def host_np(t):
@@ -499,15 +542,23 @@ def run_gpu(args, world, rank, local):
         rc, _, _ = measure_workload(htd, torch, lib, cname, ch, st_, wu_, flush, stream, dev,
                                     peaks, profile=True)
         configs[wl] = rc
+    if not args.no_hindex:
+        for wl in ("er_n2000_h2", "dcsbm_n200k_h2"):
+            cname, ch = WORKLOADS[wl]
+            configs[wl + "_hindex"] = measure_hindex(htd, torch, cname, ch)
     if not args.no_batched:
-        # the same batch under the two schedules: unions peeled round by round, and one
-        # block per graph with all rounds inside one persistent launch
-        configs["batched_4096"] = measure_batched(htd, torch, BATCHED["count"], BATCHED["seed"],
-                                                  BATCHED["steps"], BATCHED["warmup"], stream, flush,
-                                                  flags=htd.HTD_OPT_BATCH_BLOCKS)
+        # the batch as unions peeled round by round (one call), and with the autotuner's
+        # schedule per group (one block per small graph in one persistent launch, unions of
+        # tuned size and round variant for the rest)
         configs["batched_4096_unions"] = measure_batched(htd, torch, BATCHED["count"],
                                                          BATCHED["seed"], BATCHED["steps"],
                                                          BATCHED["warmup"], stream, flush)
+        from paper_2411_06405_gb300 import autotune
+
+        if os.path.exists(autotune.TABLE_PATH):
+            configs["batched_4096_tuned"] = measure_batched(
+                htd, torch, BATCHED["count"], BATCHED["seed"], BATCHED["steps"], BATCHED["warmup"],
+                stream, flush, table=autotune.load(autotune.TABLE_PATH))
     if not args.no_served:
         configs["served_poisson"] = measure_served(htd, SERVED["count"], SERVED["seed"],
                                                    SERVED["rate"], SERVED["workers"],
@@ -576,6 +627,7 @@ def main():
                     help="skip the other single-GPU workloads' entries")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream entry")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched entry")
+    ap.add_argument("--no-hindex", action="store_true", help="skip the H-index engine entries")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if world > 1:

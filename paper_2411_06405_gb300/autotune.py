@@ -119,6 +119,35 @@ def decompose(graphs, table=None, device=None):
     return out, {f"{cap}/{flags}": len(idx) for (cap, flags), idx in parts.items()}
 
 
+def prepare(graphs, table=None, device=None):
+    """Splits a batch by the table's settings and puts each part on the device once:
+    returns a list of (BatchInput, input indices, max_union_vertices, flags)."""
+    import paper_2411_06405_gb300 as htd
+
+    table = table or {}
+    parts = defaultdict(list)
+    for i, g in enumerate(graphs):
+        ent = table.get(group_key(*g), DEFAULT)
+        parts[(int(ent["max_union_vertices"]), int(ent["flags"]))].append(i)
+    return [(htd.BatchInput([graphs[i] for i in idx], device), idx, cap, flags)
+            for (cap, flags), idx in sorted(parts.items())]
+
+
+def run_prepared(prepared, count: int):
+    """Decomposes a prepared batch; returns (results in input order, summed stats)."""
+    import paper_2411_06405_gb300 as htd
+
+    out = [None] * count
+    tot = defaultdict(int)
+    for b, idx, cap, flags in prepared:
+        res, st = htd.htd_truss_decompose_batched(b, flags=flags, max_union_vertices=cap)
+        for i, r in zip(idx, res):
+            out[i] = r
+        for k in ("rounds", "unions", "rounds_rebuilt"):
+            tot[k] += st[k]
+    return out, dict(tot)
+
+
 TABLE_PATH = __import__("os").path.join(__import__("os").path.dirname(__file__), "tuning",
                                         "batched_gb300.json")
 

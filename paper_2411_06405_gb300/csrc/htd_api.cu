@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -24,6 +26,20 @@ constexpr int kRoundsPerGraph = 16;
 }  // namespace
 
 void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+cudaError_t raise_smem_limit(const void *func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = limit[{dev, func}];
+    if (cur >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 GraphDev *graph_dev(htd_graph *g) { return &g->H.g; }
 void add_launches(int64_t k) { g_launches += k; }
 

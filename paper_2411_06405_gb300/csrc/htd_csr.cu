@@ -334,9 +334,7 @@ htd_status build_csr_device(int32_t n, const int32_t *src, const int32_t *dst, i
                                               counters + 1);
         k_row_sort_block<<<nsm * 4, kBlock, 0, s>>>(lists, counters, off, colraw, deg_new);
         if (smem_big > 48 * 1024) {
-            HTD_TRY(cudaFuncSetAttribute(k_row_sort_bitset,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_big));
+            HTD_TRY(raise_smem_limit((const void *)k_row_sort_bitset, smem_big));
         }
         k_row_sort_bitset<<<nsm, kBlock, smem_big, s>>>(lists + nn, counters + 1, off, colraw,
                                                         deg_new, W);

@@ -288,8 +288,8 @@ htd_status hindex_run(htd_graph *G, Handle *H, int32_t h, int32_t sweeps, int32_
     HX_CHECK(cudaEventCreate(&t0));
     HX_CHECK(cudaEventCreate(&t1));
     HX_CHECK(cudaEventRecord(t0, s));
-    HX_CHECK(cudaFuncSetAttribute(k_hx_balls<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    HX_CHECK(cudaFuncSetAttribute(k_hx_balls<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HX_CHECK(raise_smem_limit((const void *)k_hx_balls<0>, smem));
+    HX_CHECK(raise_smem_limit((const void *)k_hx_balls<1>, smem));
     HX_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hx_balls<1>, kBlock, smem));
     if (occ < 1) {
         set_last_error("htd_hindex_decompose: an n-bit set does not fit in shared memory");

@@ -112,6 +112,11 @@ struct Handle {
 };
 
 void set_last_error(const std::string &msg);
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the current device.
+// The limit is a process-wide property of the function: it is only ever raised (under a
+// lock), so that a call for a small graph in one thread cannot lower it below what a
+// launch for a large graph in another thread needs.
+cudaError_t raise_smem_limit(const void *func, size_t bytes);
 // Adds kernels launched outside the handle calls to the thread's launch counter.
 void add_launches(int64_t k);
 

@@ -657,14 +657,10 @@ htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) 
     w.Wpad = (w.W + 3) & ~3;
     w.smem_ball = (size_t)w.Wpad * 4;
     w.smem_hsup = (size_t)w.Wpad * 4;
-    HTD_CHECK(cudaFuncSetAttribute(k_ball<kModeCount>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)w.smem_ball));
-    HTD_CHECK(cudaFuncSetAttribute(k_ball<kModeStore>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)w.smem_ball));
-    HTD_CHECK(cudaFuncSetAttribute(k_ball<kModeRebuild>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w.smem_ball));
-    HTD_CHECK(cudaFuncSetAttribute(k_hsup, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)w.smem_hsup));
+    HTD_CHECK(raise_smem_limit((const void *)k_ball<kModeCount>, w.smem_ball));
+    HTD_CHECK(raise_smem_limit((const void *)k_ball<kModeStore>, w.smem_ball));
+    HTD_CHECK(raise_smem_limit((const void *)k_ball<kModeRebuild>, w.smem_ball));
+    HTD_CHECK(raise_smem_limit((const void *)k_hsup, w.smem_hsup));
     int occ_ball = 0, occ_hsup = 0;
     HTD_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ball, k_ball<kModeRebuild>,
                                                             kBlock, w.smem_ball));
