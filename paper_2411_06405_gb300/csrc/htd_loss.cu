@@ -87,6 +87,8 @@ struct LossArgs {
     int32_t lost2_max;
     int32_t c3items_cap;
     int4 *c3items;
+    int32_t *win;       // next-frontier window buffers (2 x win_cap), null: not collected
+    int32_t win_cap;
 };
 
 __device__ __forceinline__ unsigned long long pair_key(int p, int q) {
@@ -1009,6 +1011,67 @@ __device__ void ph_apply2(const LossArgs &a) {
     if ((threadIdx.x & 31) == 0 && real) atomicAdd((unsigned long long *)&st->st_lost2, real);
 }
 
+// One candidate edge per lane (p: it joins the frontier): warp-aggregated frontier slot,
+// removal (Algorithm 1, lines 8-10) and the detection items of its two edge sides.  Whole
+// warps call it.
+__device__ __forceinline__ void select_one(const LossArgs &a, DevStatus *st, bool p, int e, int k,
+                                           int round) {
+    const int lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(0xffffffffu, p);
+    if (bal == 0u) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&st->nF, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const int pos = base + __popc(bal & lanemask_lt());
+    int u_eu = 0, u_ev = 0, rb_u = 0, re_u = 0, rb_v = 0, re_v = 0, n0 = 0, n1 = 0;
+    if (p) {
+        a.frontier_w[pos] = e;
+        remove_edge(e, k, round, a.eu, a.ev, a.slot_lo, a.slot_hi, a.sup, a.truss,
+                    a.stamp_w, a.col_live_w, a.deg_alive_w, a.hub_slot, a.hub_bits_w, a.Wpad);
+        u_eu = a.eu[e];
+        u_ev = a.ev[e];
+        rb_u = a.row_ptr[u_eu];
+        re_u = a.row_ptr[u_eu + 1];
+        rb_v = a.row_ptr[u_ev];
+        re_v = a.row_ptr[u_ev + 1];
+        // side 0: eu with {ev} and N_old(ev); side 1: ev with N_old(eu); h = 1: {eu,ev}
+        n0 = (a.h < 2) ? 1 : (re_v - rb_v + 1 + 31) >> 5;
+        n1 = (a.h < 2) ? 0 : (re_u - rb_u + 31) >> 5;
+    }
+    int incl = n0 + n1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    int ibase = 0;
+    if (lane == 31 && tot) ibase = atomicAdd(&st->npitems, tot);
+    ibase = __shfl_sync(0xffffffffu, ibase, 31);
+    const int first = ibase + incl - (n0 + n1);
+    if (p && first + n0 > a.pitems_cap) overflow_at(a, st, 2 * pos);
+    if (p && n1 && first + n0 + n1 > a.pitems_cap) overflow_at(a, st, 2 * pos + 1);
+    unsigned todo = __ballot_sync(0xffffffffu, p);
+    while (todo) {
+        const int l = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int f = __shfl_sync(0xffffffffu, first, l);
+        const int c0 = __shfl_sync(0xffffffffu, n0, l), c1 = __shfl_sync(0xffffffffu, n1, l);
+        const int pl = __shfl_sync(0xffffffffu, pos, l);
+        const int xu = __shfl_sync(0xffffffffu, u_eu, l), xv = __shfl_sync(0xffffffffu, u_ev, l);
+        const int su = __shfl_sync(0xffffffffu, rb_u, l), sv0 = __shfl_sync(0xffffffffu, rb_v, l);
+        const bool fits0 = f + c0 <= a.pitems_cap, fits1 = f + c0 + c1 <= a.pitems_cap;
+        for (int c = lane; c < c0 + c1 && f + c < a.pitems_cap; c += 32) {
+            if (c < c0)
+                a.pitems[f + c] = fits0 ? make_int4(2 * pl, sv0 - 1 + 32 * c, xu, xv)
+                                        : make_int4(-1, 0, 0, 0);
+            else
+                a.pitems[f + c] = fits1 ? make_int4(2 * pl + 1, su + 32 * (c - c0), xv, xu)
+                                        : make_int4(-1, 0, 0, 0);
+        }
+    }
+}
+
 // Phase 1 of an incremental round: every alive edge with h-support <= k-2 joins F and is
 // removed at once (Algorithm 1, lines 7-10), and the loss detection items of its two edge
 // sides are written.  A continued round only writes the items of its remaining sides.
@@ -1020,6 +1083,19 @@ __device__ void ph_select_items(const LossArgs &a) {
     }
     const int k = vload(st->k), round = vload(st->round), thr = k - 2;
     const int lane = threadIdx.x & 31;
+    if (a.win && vload(st->win_ok)) {
+        // every candidate of this round is in the window list of the last reduction
+        const int rd = vload(st->win_rd);
+        const int cnt = min(vload(st->nwin[rd]), a.win_cap);
+        const int32_t *list = a.win + (int64_t)rd * a.win_cap;
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long *)&st->st_win_selects, 1ull);
+        for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < cnt; i0 += gridDim.x * blockDim.x) {
+            const int i = i0 + lane;
+            const int e = i < cnt ? list[i] : 0;
+            select_one(a, st, i < cnt && a.sup[e] <= thr, e, k, round);
+        }
+        return;
+    }
     const int64_t stride = 16 * (int64_t)gridDim.x * blockDim.x;
     // four 16-byte loads per thread per step (16 supports), issued before any is used
     for (int64_t e0 = 16 * (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)); e0 < a.m;
@@ -1035,66 +1111,11 @@ __device__ void ph_select_items(const LossArgs &a) {
         }
 #pragma unroll
         for (int jj = 0; jj < 16; jj++) {
-            const int j = jj;
             const int e = (int)(e0 + 4 * (32 * (jj >> 2) + lane) + (jj & 3));
-            const bool p = sv[j] <= thr;
-            const unsigned bal = __ballot_sync(0xffffffffu, p);
-            if (bal == 0u) continue;
-            int base = 0;
-            if (lane == 0) base = atomicAdd(&st->nF, __popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            const int pos = base + __popc(bal & lanemask_lt());
-            int u_eu = 0, u_ev = 0, rb_u = 0, re_u = 0, rb_v = 0, re_v = 0, n0 = 0, n1 = 0;
-            if (p) {
-                a.frontier_w[pos] = e;
-                remove_edge(e, k, round, a.eu, a.ev, a.slot_lo, a.slot_hi, a.sup, a.truss,
-                            a.stamp_w, a.col_live_w, a.deg_alive_w, a.hub_slot, a.hub_bits_w, a.Wpad);
-                u_eu = a.eu[e];
-                u_ev = a.ev[e];
-                rb_u = a.row_ptr[u_eu];
-                re_u = a.row_ptr[u_eu + 1];
-                rb_v = a.row_ptr[u_ev];
-                re_v = a.row_ptr[u_ev + 1];
-                // side 0: eu with {ev} and N_old(ev); side 1: ev with N_old(eu); h = 1: {eu,ev}
-                n0 = (a.h < 2) ? 1 : (re_v - rb_v + 1 + 31) >> 5;
-                n1 = (a.h < 2) ? 0 : (re_u - rb_u + 31) >> 5;
-            }
-            int incl = n0 + n1;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const int tot = __shfl_sync(0xffffffffu, incl, 31);
-            int ibase = 0;
-            if (lane == 31 && tot) ibase = atomicAdd(&st->npitems, tot);
-            ibase = __shfl_sync(0xffffffffu, ibase, 31);
-            const int first = ibase + incl - (n0 + n1);
-            if (p && first + n0 > a.pitems_cap) overflow_at(a, st, 2 * pos);
-            if (p && n1 && first + n0 + n1 > a.pitems_cap) overflow_at(a, st, 2 * pos + 1);
-            unsigned todo = __ballot_sync(0xffffffffu, p);
-            while (todo) {
-                const int l = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const int f = __shfl_sync(0xffffffffu, first, l);
-                const int c0 = __shfl_sync(0xffffffffu, n0, l), c1 = __shfl_sync(0xffffffffu, n1, l);
-                const int pl = __shfl_sync(0xffffffffu, pos, l);
-                const int xu = __shfl_sync(0xffffffffu, u_eu, l), xv = __shfl_sync(0xffffffffu, u_ev, l);
-                const int su = __shfl_sync(0xffffffffu, rb_u, l), sv0 = __shfl_sync(0xffffffffu, rb_v, l);
-                const bool fits0 = f + c0 <= a.pitems_cap, fits1 = f + c0 + c1 <= a.pitems_cap;
-                for (int c = lane; c < c0 + c1 && f + c < a.pitems_cap; c += 32) {
-                    if (c < c0)
-                        a.pitems[f + c] = fits0 ? make_int4(2 * pl, sv0 - 1 + 32 * c, xu, xv)
-                                                : make_int4(-1, 0, 0, 0);
-                    else
-                        a.pitems[f + c] = fits1 ? make_int4(2 * pl + 1, su + 32 * (c - c0), xv, xu)
-                                                : make_int4(-1, 0, 0, 0);
-                }
-            }
+            select_one(a, st, sv[jj] <= thr, e, k, round);
         }
     }
 }
-
 // Programmatic dependent launch: a phase kernel may be scheduled while the previous one
 // still runs; it waits here until that grid has completed and its writes are visible, then
 // lets the next phase be scheduled in turn.  (Without a programmatic launch the wait
@@ -1132,7 +1153,7 @@ __global__ void __launch_bounds__(kBlock) k_loss_apply_reduce(LossArgs a) {
     if (round_idle(a)) return;
     ph_apply(a);
     if (a.h3) ph_apply2(a);
-    minreduce_body<kBlock / 32>(a.sup, a.m, a.st, 0);
+    minreduce_body<kBlock / 32>(a.sup, a.m, a.st, 0, a.win, a.win_cap);
 }
 
 constexpr int kPBlock = 512;  // threads per block of the persistent kernel
@@ -1231,6 +1252,8 @@ LossArgs loss_args(Handle *H) {
     a.lost2_max = (int32_t)w.lost2_max;
     a.c3items_cap = (int32_t)w.c3items_cap;
     a.c3items = w.c3items;
+    a.win = w.win;
+    a.win_cap = (int32_t)w.win_cap;
     return a;
 }
 

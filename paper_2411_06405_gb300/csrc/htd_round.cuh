@@ -40,7 +40,7 @@ __device__ __forceinline__ void remove_edge(int e, int k, int round, const int32
 // count): round and level bookkeeping, the next level k = max(k, min + 2) (Algorithm 1's
 // bins skip empty levels), continuation of an incremental round that ran out of room, and
 // the reset of the per-round counters.
-__device__ __forceinline__ void round_finalize(DevStatus *st, int initial) {
+__device__ __forceinline__ void round_finalize(DevStatus *st, int initial, bool window) {
     __threadfence();
     const int mn = atomicAdd(&st->min_acc, 0);
     const long long al = (long long)atomicAdd((unsigned long long *)&st->alive_acc, 0ull);
@@ -65,6 +65,16 @@ __device__ __forceinline__ void round_finalize(DevStatus *st, int initial) {
     if (!initial) st->st_slots++;
     st->alive = al;
     if (al > 0 && !unfinished) st->k = max(st->k, mn + 2);
+    // the window list just written serves the next selection if it holds every alive edge
+    // with sup <= k - 2 (it lists sup <= win_thr, and -1 marks a list that overflowed)
+    {
+        const int w = st->win_wr;
+        st->win_ok = (window && !initial && !unfinished && st->win_thr >= 0 && st->k - 2 <= st->win_thr) ? 1 : 0;
+        st->win_rd = w;
+        st->win_wr = w ^ 1;
+        st->nwin[w ^ 1] = 0;
+        st->win_thr = st->k - 2 + kWindow;
+    }
     st->min_acc = INT_MAX;
     st->alive_acc = 0;
     st->done_blocks = 0u;
@@ -85,9 +95,12 @@ __device__ __forceinline__ void round_finalize(DevStatus *st, int initial) {
 
 // Minimum alive support and alive count over all edges; the last block to finish closes the
 // round.  Every thread of every block calls it; `NW` = warps per block.
+// win (nullable): the window buffers (2 x win_cap entries); every alive edge with sup <=
+// st->win_thr is appended to buffer st->win_wr; an overflow sets win_thr to -1.
 template <int NW>
 __device__ __forceinline__ void minreduce_body(const int32_t *__restrict__ sup, int64_t m,
-                                               DevStatus *st, int initial) {
+                                               DevStatus *st, int initial,
+                                               int32_t *win = nullptr, int32_t win_cap = 0) {
     __shared__ int32_t s_min[NW];
     __shared__ long long s_cnt[NW];
     __shared__ bool s_last;
@@ -95,7 +108,9 @@ __device__ __forceinline__ void minreduce_body(const int32_t *__restrict__ sup, 
     long long lc = 0;
     // four 16-byte loads per thread per step (16 supports), issued before any is used
     const int64_t stride = 16 * (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e0 = 16 * (blockIdx.x * (int64_t)blockDim.x) + 4 * threadIdx.x; e0 < m; e0 += stride) {
+    // block-uniform trip count (the window's warp ballots need every lane)
+    for (int64_t b0 = 16 * (blockIdx.x * (int64_t)blockDim.x); b0 < m; b0 += stride) {
+        const int64_t e0 = b0 + 4 * threadIdx.x;
         int4 v[4];
 #pragma unroll
         for (int j = 0; j < 4; j++) {
@@ -117,6 +132,27 @@ __device__ __forceinline__ void minreduce_body(const int32_t *__restrict__ sup, 
                 if (sv[c] != INT_MAX) {
                     lmin = min(lmin, sv[c]);
                     lc++;
+                }
+            }
+            if (win) {
+                // window candidates of this quad, one atomic per warp
+                const int thr = *(volatile int32_t *)&st->win_thr;
+                const int64_t e = e0 + 4 * (int64_t)j * blockDim.x;
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const bool p = sv[c] <= thr;  // removed edges hold INT_MAX
+                    const unsigned bal = __ballot_sync(0xffffffffu, p);
+                    if (bal == 0u) continue;
+                    const int lane = threadIdx.x & 31;
+                    const int wb = *(volatile int32_t *)&st->win_wr;
+                    int base = 0;
+                    if (lane == __ffs(bal) - 1) base = atomicAdd(&st->nwin[wb], __popc(bal));
+                    base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+                    const int pos = base + __popc(bal & lanemask_lt());
+                    if (p) {
+                        if (pos < win_cap) win[(int64_t)wb * win_cap + pos] = (int32_t)(e + c);
+                        else atomicExch(&st->win_thr, -1);
+                    }
                 }
             }
         }
@@ -143,7 +179,7 @@ __device__ __forceinline__ void minreduce_body(const int32_t *__restrict__ sup, 
         s_last = (ticket == gridDim.x - 1);
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) round_finalize(st, initial);
+    if (s_last && threadIdx.x == 0) round_finalize(st, initial, win != nullptr);
     __syncthreads();
 }
 
