@@ -38,10 +38,10 @@ WORKLOADS = {
 CONFIG_ENTRIES = ["er_n2000_h2", "dcsbm_n200k_h2", "dcsbm_n200k_h3"]
 CONFIG_STEPS = {"dcsbm_n200k_h3": (1, 0)}  # (timed steps, warm-up steps); default (3, 1)
 # batched form: 4,096 graphs, n ~ U[50, 5000], ER or BA, h ~ U{2,3}
-BATCHED = {"count": 4096, "seed": 0x48545258, "steps": 2, "warmup": 1}
+BATCHED = {"count": 4096, "seed": 0x48545258, "steps": 1, "warmup": 1}
 # served stream: Poisson arrivals at 200 requests/s over R-MAT and BA graphs, h in {2, 3}
 # (the largest pool members are capped so that the stream finishes within the bench run)
-SERVED = {"count": 200, "seed": 0x48545259, "rate": 200.0, "workers": 4,
+SERVED = {"count": 120, "seed": 0x48545259, "rate": 200.0, "workers": 8,
           "rmat_scales": (10, 15), "ba_n": (1_000, 50_000)}
 METRIC = "edges decomposed/sec"
 UNIT = "edges/s"

@@ -11,9 +11,13 @@
 // (lexicographic) edge order is its members' canonical orders one after the other, so
 // every member's result is a contiguous slice of the union's output.
 #include <algorithm>
+#include <condition_variable>
 #include <cstdint>
 #include <cstring>
 #include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "htd_internal.h"
@@ -23,6 +27,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int32_t kDefaultUnionVertices = 1 << 18;
+constexpr int kBatchWorkers = 8;  // unions peeled at the same time (each on its own stream)
 constexpr int64_t kMaxUnionPairs = ((int64_t)1 << 30) - 1;  // 2 m_in < 2^31
 
 // One member graph of a union: its input pairs [pair_begin, pair_begin + count) land at
@@ -320,27 +325,112 @@ extern "C" htd_status htd_truss_decompose_batched(
                                            max_union_vertices, &lplan, &large);
         if (ps3 != HTD_OK) return ps3;
     }
-    for (const UnionPlan &up : (blocks ? lplan : plan)) {
-        UnionScratch U;
+    // unions are independent peels: build them all, then peel them concurrently on worker
+    // threads with their own streams (each peel's rounds are latency-bound and leave most
+    // of the GPU idle), as many at once as their footprint estimates fit the free memory
+    const std::vector<UnionPlan> &uplan = blocks ? lplan : plan;
+    struct Built {
+        std::unique_ptr<UnionScratch> U;
+        int64_t mu = 0, out = 0, est = 0;
+        int32_t h = 0;
+        htd_stats st{};
+        htd_status rc = HTD_OK;
+        std::string err;
+    };
+    std::vector<Built> built(uplan.size());
+    for (size_t u = 0; u < uplan.size(); u++) {
+        const UnionPlan &up = uplan[u];
+        Built &B = built[u];
+        B.U = std::make_unique<UnionScratch>();
         std::vector<int64_t> b, t;
-        int64_t mu = 0;
-        htd_status st = build_union(up, src_dev, dst_dev, stream, &U, &mu, &b, &t, true);
+        const htd_status st = build_union(up, src_dev, dst_dev, stream, B.U.get(), &B.mu, &b, &t, true);
         if (st != HTD_OK) return st;
-        if (mu > 0) {
-            htd_stats us;
-            std::memset(&us, 0, sizeof(us));
-            st = htd_truss_decompose_ex(U.g, up.h, flags & ~HTD_OPT_BATCH_BLOCKS, truss_dev + out_pos,
-                                        nullptr, &us, stream);
-            if (st != HTD_OK) return st;
-            add_stats(&acc, us);
-            if (!us.incremental) acc.incremental = 0;
-            unions++;
-        }
         for (size_t j = 0; j < up.mem.size(); j++) {
             out_offsets[up.ids[j]] = out_pos + b[j];
             out_m[up.ids[j]] = t[j] - b[j];
         }
-        out_pos += mu;
+        B.out = out_pos;
+        B.h = up.h;
+        out_pos += B.mu;
+    }
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        set_last_error("htd_truss_decompose_batched: cudaMemGetInfo failed");
+        return HTD_ECUDA;
+    }
+    const int64_t budget = (int64_t)(0.8 * (double)free_b);
+    for (size_t u = 0; u < uplan.size(); u++)
+        built[u].est = htd_footprint_estimate((int32_t)uplan[u].n, uplan[u].pairs, uplan[u].h, budget);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaEvent_t ev_start = nullptr;
+    if (cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev_start, s) != cudaSuccess) {
+        set_last_error("htd_truss_decompose_batched: event on the caller's stream failed");
+        if (ev_start) cudaEventDestroy(ev_start);
+        return HTD_ECUDA;
+    }
+    const int nworkers = (int)std::min<size_t>(kBatchWorkers, std::max<size_t>(1, uplan.size()));
+    std::mutex mu;
+    std::condition_variable cv;
+    int64_t used = 0;
+    int running = 0;
+    size_t next = 0;
+    auto worker = [&](int wid) {
+        (void)wid;
+        cudaSetDevice(dev);
+        cudaStream_t ws = nullptr;
+        if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) ws = nullptr;
+        if (ws) cudaStreamWaitEvent(ws, ev_start, 0);
+        for (;;) {
+            size_t i;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                if (next >= built.size()) break;
+                i = next++;
+                Built &B = built[i];
+                if (B.mu == 0) continue;
+                // admission: wait until the estimate fits beside the running peels (a peel
+                // larger than the whole budget runs alone)
+                cv.wait(lk, [&] { return used + B.est <= budget || running == 0; });
+                used += B.est;
+                running++;
+            }
+            Built &B = built[i];
+            if (!ws) {
+                B.rc = HTD_ECUDA;
+                B.err = "htd_truss_decompose_batched: worker stream creation failed";
+            } else {
+                B.rc = htd_truss_decompose_ex(B.U->g, B.h, flags & ~HTD_OPT_BATCH_BLOCKS, truss_dev + B.out,
+                                              nullptr, &B.st, ws);
+                if (B.rc != HTD_OK) B.err = htd_last_error();
+            }
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                used -= B.est;
+                running--;
+            }
+            cv.notify_all();
+        }
+        if (ws) {
+            cudaStreamSynchronize(ws);
+            cudaStreamDestroy(ws);
+        }
+    };
+    std::vector<std::thread> threads;
+    for (int w = 1; w < nworkers; w++) threads.emplace_back(worker, w);
+    worker(0);
+    for (auto &t : threads) t.join();
+    cudaEventDestroy(ev_start);
+    for (Built &B : built) {
+        if (B.mu == 0) continue;
+        if (B.rc != HTD_OK) {
+            set_last_error(B.err);
+            return B.rc;
+        }
+        add_stats(&acc, B.st);
+        if (!B.st.incremental) acc.incremental = 0;
+        unions++;
     }
     if (num_unions) *num_unions = unions;
     if (stats) *stats = acc;

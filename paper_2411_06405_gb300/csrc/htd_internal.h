@@ -82,6 +82,7 @@ struct PeelWork {
     int64_t lost2_cap = 0;
     int64_t lost2_max = 0;
     int4 *lost2 = nullptr;         // (min, max, hash slot, 0) per radius-2 lost pair
+    int32_t *touch2 = nullptr;     // n: round in which the vertex last lost a radius-2 member
     int4 *c3items = nullptr;       // radius-3 candidate items of a round
     int64_t c3items_cap = 0;
     int32_t *win = nullptr;        // next-frontier window lists (2 x win_cap)

@@ -89,6 +89,7 @@ struct LossArgs {
     int4 *c3items;
     int32_t *win;       // next-frontier window buffers (2 x win_cap), null: not collected
     int32_t win_cap;
+    int32_t *touch2;    // h = 3: round in which the vertex last lost a radius-2 member
 };
 
 __device__ __forceinline__ unsigned long long pair_key(int p, int q) {
@@ -449,6 +450,12 @@ __device__ __forceinline__ void record_lost_warp(const LossArgs &a, DevStatus *s
             }
             lostv[idx] = rec;
             if (rec.x >= 0) rec_idx = idx;
+            if (r2) {
+                // B2_new(v) differs from the stored B2(v) only at vertices marked here
+                const int round = vload(st->round);
+                a.touch2[x] = round;
+                a.touch2[z] = round;
+            }
         }
     }
     if (r2) return;  // radius-2 losses change no support directly
@@ -781,11 +788,15 @@ __device__ __forceinline__ bool lost2_now(const LossArgs &a, int p, int q, unsig
     return false;
 }
 
-// q in B2_new(z): the stored radius-2 bit, unless this round lost the pair.
-__device__ __forceinline__ bool in_b2_new(const LossArgs &a, int z, int q, unsigned &bytes) {
+// q in B2_new(z): the stored radius-2 bit, unless this round lost the pair (the pair set is
+// probed only for vertices that lost a radius-2 member this round).
+__device__ __forceinline__ bool in_b2_new(const LossArgs &a, int z, int q, int round, unsigned &bytes) {
     bytes += 4;
     if (!((a.pool2[(int64_t)z * a.Wpad + (q >> 5)] >> (q & 31)) & 1u)) return false;
-    return z == q || !lost2_now(a, z, q, bytes);
+    if (z == q) return true;
+    bytes += 4;
+    if (a.touch2[z] != round) return true;
+    return !lost2_now(a, z, q, bytes);
 }
 
 // Words of a B2 row one radius-3 candidate item scans.
@@ -849,7 +860,7 @@ __device__ void ph_c3_items(const LossArgs &a) {
 // endpoint whose alive row is walked, t the other one; the pair is kept at the first alive
 // neighbour y of w with t in B2_new(y).  The rows are laid end to end and walked 128 slots
 // per step as in warp_hard_pairs.  Called by whole warps.
-__device__ __forceinline__ void warp_walk3(const LossArgs &a, int &state, int w, int t,
+__device__ __forceinline__ void warp_walk3(const LossArgs &a, int &state, int w, int t, int round,
                                            unsigned &reads) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -885,7 +896,7 @@ __device__ __forceinline__ void warp_walk3(const LossArgs &a, int &state, int w,
             const int to = __shfl_sync(full, t, own[j]);
             if (y[j] >= 0) {
                 reads++;
-                if (in_b2_new(a, y[j], to, reads)) hits |= 1u << own[j];
+                if (in_b2_new(a, y[j], to, round, reads)) hits |= 1u << own[j];
             }
         }
         hits = __reduce_or_sync(full, hits);
@@ -897,12 +908,12 @@ __device__ __forceinline__ void warp_walk3(const LossArgs &a, int &state, int w,
 
 // Tests the lanes' radius-3 candidate pairs {p,q} (q < 0: none; q is in B3_old(p)) in the
 // new graph and records the lost ones with their support-update items.  Whole warps.
-__device__ __forceinline__ void test_pairs3(const LossArgs &a, DevStatus *st, int p, int q,
+__device__ __forceinline__ void test_pairs3(const LossArgs &a, DevStatus *st, int p, int q, int round,
                                             unsigned &reads, unsigned long long &pairs) {
     int state = kKept, w = p, t = q;
     if (q >= 0) {
         pairs++;
-        if (!in_b2_new(a, p, q, reads)) {
+        if (!in_b2_new(a, p, q, round, reads)) {
             state = kHard;
             reads += 2;
             if (a.deg_alive[q] < a.deg_alive[p]) {  // walk the shorter alive row
@@ -911,7 +922,7 @@ __device__ __forceinline__ void test_pairs3(const LossArgs &a, DevStatus *st, in
             }
         }
     }
-    if (__any_sync(0xffffffffu, state == kHard)) warp_walk3(a, state, w, t, reads);
+    if (__any_sync(0xffffffffu, state == kHard)) warp_walk3(a, state, w, t, round, reads);
     record_lost_warp(a, st, state == kLost, p, q, 0, reads);
 }
 
@@ -956,7 +967,7 @@ __device__ void ph_test3(const LossArgs &a) {
                     q = wbase + __ffs(bits) - 1;
                     bits &= bits - 1u;
                 }
-                test_pairs3(a, st, x, q, reads, pairs);
+                test_pairs3(a, st, x, q, round, reads, pairs);
             }
         } else {
             // {x} x N_old(y) for the slots of the item, restricted to B3_old(x)
@@ -970,7 +981,7 @@ __device__ void ph_test3(const LossArgs &a) {
                     if ((a.pool[(int64_t)x * a.Wpad + (c >> 5)] >> (c & 31)) & 1u) q = c;
                 }
             }
-            test_pairs3(a, st, x, q, reads, pairs);
+            test_pairs3(a, st, x, q, round, reads, pairs);
         }
         reads_total += reads;
     }
@@ -1254,6 +1265,7 @@ LossArgs loss_args(Handle *H) {
     a.c3items = w.c3items;
     a.win = w.win;
     a.win_cap = (int32_t)w.win_cap;
+    a.touch2 = w.touch2;
     return a;
 }
 

@@ -631,6 +631,7 @@ void free_work(PeelWork *w) {
     cudaFree(w->lost2_keys);
     cudaFree(w->lost2);
     cudaFree(w->c3items);
+    cudaFree(w->touch2);
     cudaFree(w->win);
     cudaFree(w->status);
     if (w->status_host) cudaFreeHost(w->status_host);
@@ -728,6 +729,7 @@ htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) 
             HTD_CHECK(alloc_n(&w.ball_meta2, n));
             HTD_CHECK(alloc_n(&w.changed_list2, n));
             HTD_CHECK(alloc_n(&w.changed_stamp2, n));
+            HTD_CHECK(alloc_n(&w.touch2, n));
             int64_t cap2 = 4096;
             while (cap2 < 4 * m && cap2 < ((int64_t)1 << 22)) cap2 <<= 1;
             if (tiny_table) cap2 = 128;
@@ -804,6 +806,7 @@ htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
         if (w.inc3) {
             HTD_CHECK(cudaMemsetAsync(w.lost2_keys, 0xff, w.lost2_cap * sizeof(unsigned long long), s));
             HTD_CHECK(cudaMemsetAsync(w.changed_stamp2, 0xff, (n > 0 ? n : 1) * sizeof(int32_t), s));
+            HTD_CHECK(cudaMemsetAsync(w.touch2, 0xff, (n > 0 ? n : 1) * sizeof(int32_t), s));
         }
         if (w.nhub > 0) {
             k_hub_init<<<std::min(w.nhub, H->num_sms * 8), kBlock, 0, s>>>(w.hub_list, w.nhub, g.row_ptr,
