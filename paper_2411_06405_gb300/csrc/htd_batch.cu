@@ -353,6 +353,13 @@ extern "C" htd_status htd_truss_decompose_batched(
         B.h = up.h;
         out_pos += B.mu;
     }
+    bool any = false;
+    for (const Built &B : built) any = any || B.mu > 0;
+    if (!any) {
+        if (num_unions) *num_unions = unions;
+        if (stats) *stats = acc;
+        return HTD_OK;
+    }
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
         set_last_error("htd_truss_decompose_batched: cudaMemGetInfo failed");
