@@ -365,7 +365,7 @@ extern "C" htd_status htd_truss_decompose_batched(
         set_last_error("htd_truss_decompose_batched: cudaMemGetInfo failed");
         return HTD_ECUDA;
     }
-    const int64_t budget = (int64_t)(0.8 * (double)free_b);
+    const int64_t budget = (int64_t)(0.7 * (double)free_b);
     for (size_t u = 0; u < uplan.size(); u++)
         built[u].est = htd_footprint_estimate((int32_t)uplan[u].n, uplan[u].pairs, uplan[u].h, budget);
     int dev = 0;
@@ -431,6 +431,13 @@ extern "C" htd_status htd_truss_decompose_batched(
     cudaEventDestroy(ev_start);
     for (Built &B : built) {
         if (B.mu == 0) continue;
+        if (B.rc == HTD_ENOMEM) {
+            // out of memory beside the other peels: once more, alone, on the caller's stream
+            std::memset(&B.st, 0, sizeof(B.st));
+            B.rc = htd_truss_decompose_ex(B.U->g, B.h, flags & ~HTD_OPT_BATCH_BLOCKS, truss_dev + B.out,
+                                          nullptr, &B.st, stream);
+            if (B.rc != HTD_OK) B.err = htd_last_error();
+        }
         if (B.rc != HTD_OK) {
             set_last_error(B.err);
             return B.rc;

@@ -638,8 +638,34 @@ void free_work(PeelWork *w) {
     *w = PeelWork{};
 }
 
-// Allocates (or reuses) the scratch of an h-support pass / peel at hop threshold h.
+void drop_graphs(Handle *H);
+namespace {
+htd_status ensure_work_impl(Handle *H, int32_t h, bool incremental, bool tiny_table);
+}  // namespace
+
+// The captured round graphs hold the scratch pointers: dropped whenever the scratch goes.
+void drop_graphs(Handle *H) {
+    if (H->graph_exec) cudaGraphExecDestroy(H->graph_exec);
+    if (H->graph_exec_timed) cudaGraphExecDestroy(H->graph_exec_timed);
+    H->graph_exec = nullptr;
+    H->graph_exec_timed = nullptr;
+    H->graph_h = 0;
+    H->graph_rounds = 0;
+}
+
+// Allocates (or reuses) the scratch of an h-support pass / peel; on failure nothing of it
+// is kept (the handle stays usable for a later attempt).
 htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) {
+    const htd_status st = ensure_work_impl(H, h, incremental, tiny_table);
+    if (st != HTD_OK) {
+        drop_graphs(H);
+        free_work(&H->w);
+    }
+    return st;
+}
+
+namespace {
+htd_status ensure_work_impl(Handle *H, int32_t h, bool incremental, bool tiny_table) {
     PeelWork &w = H->w;
     GraphDev &g = H->g;
     incremental = incremental && h <= 3;
@@ -650,6 +676,7 @@ htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) 
     }
     if (w.status) {
         // the per-block BFS lists and the ball storage depend on h: rebuild everything
+        drop_graphs(H);
         free_work(&w);
     }
     const int64_t n = g.n, m = g.m;
@@ -780,6 +807,8 @@ htd_status ensure_work(Handle *H, int32_t h, bool incremental, bool tiny_table) 
     HTD_CHECK(cudaMallocHost(reinterpret_cast<void **>(&w.status_host), sizeof(DevStatus)));
     return HTD_OK;
 }
+
+}  // namespace
 
 // Initial pass: every vertex's ball (count, reserve, store) and every edge's h-support,
 // then the first min reduction.  Leaves the status ready for round 0.

@@ -256,6 +256,11 @@ int64_t htd_footprint_estimate(int32_t n, int64_t m_in, int32_t h, int64_t free_
     } else {
         bytes += 4.0 * N * std::min(W, 64.0);
     }
+    // h >= 3: the ball builder's per-block BFS level lists (2n int32 for each of up to
+    // about 8 resident blocks on each of 152 SMs)
+    if (h >= 3) bytes += 8.0 * N * 152.0 * 8.0;
+    // h = 3 incremental: radius-3 candidate items (up to 2^25 x 16 bytes)
+    if (h == 3) bytes += 16.0 * std::min(8.0 * M, (double)(1 << 25));
     return (int64_t)bytes;
 }
 
