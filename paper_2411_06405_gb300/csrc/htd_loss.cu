@@ -272,9 +272,13 @@ __device__ __forceinline__ void warp_dense_pairs(const LossArgs &a, int &state, 
     }
 }
 
+// Slots of the concatenated rows each lane loads per step of a warp's common walk (their
+// loads are independent, so a step costs two round trips whatever the count).
+constexpr int kWalkUnroll = 8;
+
 // Common alive neighbours for the warp's hard pairs (lanes with state == kHard; p the
 // shorter row), all at once: the pairs' rows of p are laid end to end and the warp walks
-// the concatenation 128 slots per step, each lane finding the pair its slot belongs to by a
+// the concatenation 32 x kWalkUnroll slots per step, each lane finding the pair its slot belongs to by a
 // binary search over the lanes' running row lengths.  A pair is kept at its first alive
 // neighbour that q also has; the walk skips kept pairs and stops once none is pending.
 // Called by whole warps.
@@ -296,10 +300,10 @@ __device__ __forceinline__ void warp_hard_pairs(const LossArgs &a, int &state, i
     const int total = __shfl_sync(full, incl, 31);
     unsigned pending = __ballot_sync(full, hard);
     unsigned kept = 0u;
-    for (int base = 0; base < total && pending; base += 128) {
-        int y[4], own[4];
+    for (int base = 0; base < total && pending; base += 32 * kWalkUnroll) {
+        int y[kWalkUnroll], own[kWalkUnroll];
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < kWalkUnroll; j++) {
             const int idx = base + 32 * j + lane;
             // owner lane: the number of lanes whose rows end at or before idx
             int o = 0;
@@ -313,7 +317,7 @@ __device__ __forceinline__ void warp_hard_pairs(const LossArgs &a, int &state, i
         }
         unsigned hits = 0u;
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < kWalkUnroll; j++) {
             const int qo = __shfl_sync(full, q, own[j]);
             const uint32_t *qs = reinterpret_cast<const uint32_t *>(
                 __shfl_sync(full, reinterpret_cast<unsigned long long>(qset), own[j]));
@@ -1083,6 +1087,22 @@ __device__ __forceinline__ void select_one(const LossArgs &a, DevStatus *st, boo
     }
 }
 
+// Selection from the last reduction's window list (every alive edge with sup <= k - 2 is
+// in it), warp-strided from `first` over `stride` threads.
+__device__ __forceinline__ void select_from_window(const LossArgs &a, DevStatus *st, int first,
+                                                   int stride) {
+    const int k = vload(st->k), round = vload(st->round), thr = k - 2;
+    const int lane = threadIdx.x & 31;
+    const int rd = vload(st->win_rd);
+    const int cnt = min(vload(st->nwin[rd]), a.win_cap);
+    const int32_t *list = a.win + (int64_t)rd * a.win_cap;
+    for (int i0 = first + (threadIdx.x & ~31); i0 < cnt; i0 += stride) {
+        const int i = i0 + lane;
+        const int e = i < cnt ? list[i] : 0;
+        select_one(a, st, i < cnt && a.sup[e] <= thr, e, k, round);
+    }
+}
+
 // Phase 1 of an incremental round: every alive edge with h-support <= k-2 joins F and is
 // removed at once (Algorithm 1, lines 7-10), and the loss detection items of its two edge
 // sides are written.  A continued round only writes the items of its remaining sides.
@@ -1094,17 +1114,12 @@ __device__ void ph_select_items(const LossArgs &a) {
     }
     const int k = vload(st->k), round = vload(st->round), thr = k - 2;
     const int lane = threadIdx.x & 31;
+    // the block that closed the last round already selected this one from its window list
+    if (vload(st->presel_round) == round) return;
     if (a.win && vload(st->win_ok)) {
         // every candidate of this round is in the window list of the last reduction
-        const int rd = vload(st->win_rd);
-        const int cnt = min(vload(st->nwin[rd]), a.win_cap);
-        const int32_t *list = a.win + (int64_t)rd * a.win_cap;
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long *)&st->st_win_selects, 1ull);
-        for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < cnt; i0 += gridDim.x * blockDim.x) {
-            const int i = i0 + lane;
-            const int e = i < cnt ? list[i] : 0;
-            select_one(a, st, i < cnt && a.sup[e] <= thr, e, k, round);
-        }
+        select_from_window(a, st, blockIdx.x * blockDim.x, gridDim.x * blockDim.x);
         return;
     }
     const int64_t stride = 16 * (int64_t)gridDim.x * blockDim.x;
@@ -1164,7 +1179,17 @@ __global__ void __launch_bounds__(kBlock) k_loss_apply_reduce(LossArgs a) {
     if (round_idle(a)) return;
     ph_apply(a);
     if (a.h3) ph_apply2(a);
-    minreduce_body<kBlock / 32>(a.sup, a.m, a.st, 0, a.win, a.win_cap);
+    const bool closer = minreduce_body<kBlock / 32>(a.sup, a.m, a.st, 0, a.win, a.win_cap);
+    // the closing block selects the next round's frontier itself when the window holds it
+    // (the next selection launch then returns at once)
+    if (closer && vload(a.st->win_ok) && vload(a.st->alive) > 0 && vload(a.st->halt) == 0) {
+        select_from_window(a, a.st, 0, blockDim.x);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            a.st->presel_round = a.st->round;
+            atomicAdd((unsigned long long *)&a.st->st_win_selects, 1ull);
+        }
+    }
 }
 
 constexpr int kPBlock = 512;  // threads per block of the persistent kernel

@@ -97,8 +97,9 @@ __device__ __forceinline__ void round_finalize(DevStatus *st, int initial, bool 
 // round.  Every thread of every block calls it; `NW` = warps per block.
 // win (nullable): the window buffers (2 x win_cap entries); every alive edge with sup <=
 // st->win_thr is appended to buffer st->win_wr; an overflow sets win_thr to -1.
+// Returns true in the block that closed the round.
 template <int NW>
-__device__ __forceinline__ void minreduce_body(const int32_t *__restrict__ sup, int64_t m,
+__device__ __forceinline__ bool minreduce_body(const int32_t *__restrict__ sup, int64_t m,
                                                DevStatus *st, int initial,
                                                int32_t *win = nullptr, int32_t win_cap = 0) {
     __shared__ int32_t s_min[NW];
@@ -181,6 +182,7 @@ __device__ __forceinline__ void minreduce_body(const int32_t *__restrict__ sup, 
     __syncthreads();
     if (s_last && threadIdx.x == 0) round_finalize(st, initial, win != nullptr);
     __syncthreads();
+    return s_last;
 }
 
 // Barrier across all blocks of a cooperative launch (all co-resident, at most 64 x 32
