@@ -33,6 +33,7 @@ WORKLOADS = {
     "dcsbm_n200k_h3": ("dcsbm_n200k", 3),
     "er_n2000_h2": ("er_n2000", 2),
     "rmat_s16_h2": ("rmat_s16", 2),
+    "dcsbm_n50k_h3": ("dcsbm_n50k", 3),
 }
 # the other single-GPU workloads reported beside the headline (fewer steps each)
 CONFIG_ENTRIES = ["er_n2000_h2", "dcsbm_n200k_h2", "dcsbm_n200k_h3"]
@@ -544,9 +545,9 @@ def run_gpu(args, world, rank, local):
                                     peaks, profile=True)
         configs[wl] = rc
     if not args.no_hindex:
-        for wl in ("er_n2000_h2", "dcsbm_n200k_h2"):
+        for wl, sweeps in (("er_n2000_h2", (1, 8, 32)), ("dcsbm_n200k_h2", (1, 8))):
             cname, ch = WORKLOADS[wl]
-            configs[wl + "_hindex"] = measure_hindex(htd, torch, cname, ch)
+            configs[wl + "_hindex"] = measure_hindex(htd, torch, cname, ch, sweeps)
     if not args.no_batched:
         # the batch as unions peeled round by round (one call), and with the autotuner's
         # schedule per group (one block per small graph in one persistent launch, unions of

@@ -244,6 +244,13 @@ def config_graph(name: str) -> GraphSpec:
                          "DC-SBM n=200,000, 200 blocks (size exponent 2.1, min 100), theta "
                          "Pareto 2.5 capped at sqrt(n), 1,200,000 edges, 10% inter-block, "
                          "seed 0x48545257")
+    if name == "dcsbm_n50k":
+        # a quarter-size version of the DC-SBM workload (profiling runs)
+        s, d = dcsbm(50_000, 50, 2.1, 100, 2.5, 300_000, 0.10, CONFIG_SEED_BASE + 2)
+        return GraphSpec(name, 50_000, s, d, (2, 3),
+                         "DC-SBM n=50,000, 50 blocks (size exponent 2.1, min 100), theta "
+                         "Pareto 2.5 capped at sqrt(n), 300,000 edges, 10% inter-block, "
+                         "seed 0x48545257")
     if name.startswith("rmat_s"):
         scale = int(name[len("rmat_s"):])
         s, d = rmat(scale, 8, 0.57, 0.19, 0.19, CONFIG_SEED_BASE + 1)
