@@ -411,6 +411,9 @@ extern "C" htd_status htd_truss_decompose_batched(
                 B.rc = htd_truss_decompose_ex(B.U->g, B.h, flags & ~HTD_OPT_BATCH_BLOCKS, truss_dev + B.out,
                                               nullptr, &B.st, ws);
                 if (B.rc != HTD_OK) B.err = htd_last_error();
+                // the union's result is in place: its graph and peel scratch go now, so that
+                // the memory serves the unions still to come
+                else B.U.reset();
             }
             {
                 std::lock_guard<std::mutex> lk(mu);
