@@ -388,6 +388,7 @@ def measure_served(htd, count: int, seed: int, rate: float, workers: int, rmat_s
         srv.close()
     lat = np.array([i["done_s"] - i["submit_s"] for i in infos]) * 1e3
     wait = np.array([i["start_s"] - i["submit_s"] for i in infos]) * 1e3
+    service = np.array([i["done_s"] - i["start_s"] for i in infos]) * 1e3
     span = max(i["done_s"] for i in infos) - min(i["submit_s"] for i in infos)
     edges = float(sum(i["m"] for i in infos))
     return {"workload": "served_poisson", "requests": count, "offered_rate_per_s": rate,
@@ -399,6 +400,9 @@ def measure_served(htd, count: int, seed: int, rate: float, workers: int, rmat_s
                            "max": float(lat.max())},
             "queue_wait_ms": {"p50": float(np.percentile(wait, 50)),
                               "p99": float(np.percentile(wait, 99))},
+            "service_ms": {"p50": float(np.percentile(service, 50)),
+                           "p99": float(np.percentile(service, 99))},
+            "offered_over_capacity": rate * float(np.mean(service)) / 1e3 / workers,
             "peak_running": sinfo["peak_running"], "budget_bytes": sinfo["budget_bytes"],
             "peak_reserved_bytes": sinfo["peak_reserved_bytes"],
             "retries": int(sum(i["retries"] for i in infos))}

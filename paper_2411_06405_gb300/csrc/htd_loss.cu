@@ -804,7 +804,7 @@ __device__ __forceinline__ bool in_b2_new(const LossArgs &a, int z, int q, int r
 }
 
 // Words of a B2 row one radius-3 candidate item scans.
-constexpr int kC3Words = 512;
+constexpr int kC3Words = 128;
 
 // Radius-3 candidate items of the round's frontier, one warp per frontier edge (a,b):
 //   (a, row b, word range) and (b, row a, word range): {a} x B2_old(b) and {b} x B2_old(a);
