@@ -76,8 +76,6 @@ struct DevStatus {
     int32_t win_ok;            // 1: buffer win_rd holds every candidate of the next round
     int32_t win_thr;           // sup threshold of the list being written
     int64_t st_win_selects;    // selections served from the window list
-    int32_t presel_round;      // round whose frontier the closing block already selected
-    int32_t pad3;
 };
 
 constexpr int32_t kWindow = 4;

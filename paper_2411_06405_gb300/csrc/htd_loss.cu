@@ -274,7 +274,7 @@ __device__ __forceinline__ void warp_dense_pairs(const LossArgs &a, int &state, 
 
 // Slots of the concatenated rows each lane loads per step of a warp's common walk (their
 // loads are independent, so a step costs two round trips whatever the count).
-constexpr int kWalkUnroll = 8;
+constexpr int kWalkUnroll = 4;
 
 // Common alive neighbours for the warp's hard pairs (lanes with state == kHard; p the
 // shorter row), all at once: the pairs' rows of p are laid end to end and the warp walks
@@ -803,8 +803,14 @@ __device__ __forceinline__ bool in_b2_new(const LossArgs &a, int z, int q, int r
     return !lost2_now(a, z, q, bytes);
 }
 
+// Position of the k-th (0-based) set bit of v (k < popc(v)).
+__device__ __forceinline__ int nth_set_bit(uint32_t v, int k) {
+    for (; k > 0; k--) v &= v - 1u;
+    return __ffs(v) - 1;
+}
+
 // Words of a B2 row one radius-3 candidate item scans.
-constexpr int kC3Words = 128;
+constexpr int kC3Words = 32;
 
 // Radius-3 candidate items of the round's frontier, one warp per frontier edge (a,b):
 //   (a, row b, word range) and (b, row a, word range): {a} x B2_old(b) and {b} x B2_old(a);
@@ -949,28 +955,31 @@ __device__ void ph_test3(const LossArgs &a) {
         const int x = item.x, y = item.y;
         unsigned reads = 0;
         if (item.w < 0) {
-            // {x} x B2_old(y), restricted to B3_old(x): one pair per lane at a time
+            // {x} x B2_old(y), restricted to B3_old(x): lane i holds word item.z + i of the
+            // AND; the warp's candidates are dealt out 32 at a time in order
             const int w1 = -1 - item.w;
-            const uint32_t *r2 = a.pool2 + (int64_t)y * a.Wpad;
-            const uint32_t *r3 = a.pool + (int64_t)x * a.Wpad;
-            int wi = item.z + lane;
+            const int wi = item.z + lane;
             uint32_t bits = 0u;
-            int wbase = 0;
-            for (;;) {
-                while (bits == 0u && wi < w1) {
-                    bits = r2[wi] & r3[wi];
-                    reads += 2;
-                    if (wi == (x >> 5)) bits &= ~(1u << (x & 31));
-                    wbase = wi << 5;
-                    wi += 32;
-                }
-                const bool has = bits != 0u;
-                if (!__any_sync(0xffffffffu, has)) break;
+            if (wi < w1) {
+                bits = a.pool2[(int64_t)y * a.Wpad + wi] & a.pool[(int64_t)x * a.Wpad + wi];
+                reads += 2;
+                if (wi == (x >> 5)) bits &= ~(1u << (x & 31));
+            }
+            const int cnt = __popc(bits);
+            const int incl = warp_incl_scan(cnt);
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int t0 = 0; t0 < total; t0 += 32) {
+                const int idx = t0 + lane;
+                // owner lane: the number of lanes whose candidates end at or before idx
+                int o = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (__shfl_sync(0xffffffffu, incl, o + step - 1) <= idx) o += step;
+                o = min(o, 31);
+                const uint32_t ob = __shfl_sync(0xffffffffu, bits, o);
+                const int ex = __shfl_sync(0xffffffffu, incl - cnt, o);
                 int q = -1;
-                if (has) {
-                    q = wbase + __ffs(bits) - 1;
-                    bits &= bits - 1u;
-                }
+                if (idx < total) q = ((item.z + o) << 5) + nth_set_bit(ob, idx - ex);
                 test_pairs3(a, st, x, q, round, reads, pairs);
             }
         } else {
@@ -1114,8 +1123,6 @@ __device__ void ph_select_items(const LossArgs &a) {
     }
     const int k = vload(st->k), round = vload(st->round), thr = k - 2;
     const int lane = threadIdx.x & 31;
-    // the block that closed the last round already selected this one from its window list
-    if (vload(st->presel_round) == round) return;
     if (a.win && vload(st->win_ok)) {
         // every candidate of this round is in the window list of the last reduction
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long *)&st->st_win_selects, 1ull);
@@ -1179,17 +1186,7 @@ __global__ void __launch_bounds__(kBlock) k_loss_apply_reduce(LossArgs a) {
     if (round_idle(a)) return;
     ph_apply(a);
     if (a.h3) ph_apply2(a);
-    const bool closer = minreduce_body<kBlock / 32>(a.sup, a.m, a.st, 0, a.win, a.win_cap);
-    // the closing block selects the next round's frontier itself when the window holds it
-    // (the next selection launch then returns at once)
-    if (closer && vload(a.st->win_ok) && vload(a.st->alive) > 0 && vload(a.st->halt) == 0) {
-        select_from_window(a, a.st, 0, blockDim.x);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            a.st->presel_round = a.st->round;
-            atomicAdd((unsigned long long *)&a.st->st_win_selects, 1ull);
-        }
-    }
+    minreduce_body<kBlock / 32>(a.sup, a.m, a.st, 0, a.win, a.win_cap);
 }
 
 constexpr int kPBlock = 512;  // threads per block of the persistent kernel

@@ -822,7 +822,6 @@ htd_status initial_pass(Handle *H, int32_t h, cudaStream_t s, int64_t *launches,
     w.status_host->k = 2;
     w.status_host->min_acc = INT_MAX;
     w.status_host->overflow_unit = INT_MAX;
-    w.status_host->presel_round = -1;
     HTD_CHECK(cudaMemcpyAsync(w.status, w.status_host, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
     if (m > 0)
         HTD_CHECK(cudaMemcpyAsync(w.col_live, g.col, 2 * m * sizeof(int32_t),
