@@ -298,7 +298,6 @@ def measure_workload(htd, torch, lib, name, h, steps, warmup, flush, stream, dev
                                "pairs3_tested": s0["pairs3_tested"],
                                "pairs2_lost": s0["pairs2_lost"],
                                "rounds_rebuilt": s0["rounds_rebuilt"],
-                               "window_selects": s0["window_selects"],
                                "member_tests": s0["member_tests"],
                                "edge_refreshes_per_endpoint": s0["hsup_evals"] - m,
                                "alg_bytes_detect": s0["alg_bytes_detect"],

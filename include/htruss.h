@@ -99,8 +99,6 @@ typedef struct htd_stats {
     int64_t pairs2_lost;     /* incremental h = 3 rounds: pairs that left radius-2 balls */
     int64_t rounds_rebuilt;  /* incremental h = 3 rounds that ran out of room and were
                                 finished by rebuilding the candidates' balls */
-    int64_t window_selects;  /* incremental rounds whose frontier came from the previous
-                                reduction's list of edges near the level (no full scan) */
 } htd_stats;
 
 /* Option flags for htd_truss_decompose_ex. */

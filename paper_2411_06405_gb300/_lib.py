@@ -74,7 +74,6 @@ class HtdStats(ctypes.Structure):
         ("pairs3_tested", ctypes.c_int64),
         ("pairs2_lost", ctypes.c_int64),
         ("rounds_rebuilt", ctypes.c_int64),
-        ("window_selects", ctypes.c_int64),
     ]
 
     def as_dict(self):

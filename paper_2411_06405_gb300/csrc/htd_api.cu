@@ -540,7 +540,6 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
         local.pairs3_tested = s->st_c3_pairs;
         local.pairs2_lost = s->st_lost2;
         local.rounds_rebuilt = s->st_recovered;
-        local.window_selects = s->st_win_selects;
         *stats = local;
     }
     return HTD_OK;

@@ -101,7 +101,6 @@ void add_stats(htd_stats *acc, const htd_stats &s) {
     acc->pairs3_tested += s.pairs3_tested;
     acc->pairs2_lost += s.pairs2_lost;
     acc->rounds_rebuilt += s.rounds_rebuilt;
-    acc->window_selects += s.window_selects;
 }
 
 // One union of the plan: its hop threshold and members (graph ids, in input order).

@@ -66,19 +66,8 @@ struct DevStatus {
     int64_t st_c3_pairs;       // radius-3 candidate pairs tested
     int64_t st_lost2;          // radius-2 lost pairs
     int64_t st_recovered;      // rounds finished by the rebuild recovery
-    // next-frontier window: while it scans for the minimum, the reduction of an incremental
-    // round lists every alive edge with sup <= k - 2 + kWindow into buffer win_wr; if the
-    // next level is within that window, the next selection reads the list instead of every
-    // support
-    int32_t nwin[2];           // entries of each window buffer
-    int32_t win_wr;            // buffer the reductions of the current round write
-    int32_t win_rd;            // buffer the next selection reads
-    int32_t win_ok;            // 1: buffer win_rd holds every candidate of the next round
-    int32_t win_thr;           // sup threshold of the list being written
-    int64_t st_win_selects;    // selections served from the window list
 };
 
-constexpr int32_t kWindow = 4;
 
 enum : int32_t {
     kErrBallGrew = 1,        // a rebuilt ball was larger than before (cannot happen)

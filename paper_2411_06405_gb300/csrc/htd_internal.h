@@ -85,8 +85,6 @@ struct PeelWork {
     int32_t *touch2 = nullptr;     // n: round in which the vertex last lost a radius-2 member
     int4 *c3items = nullptr;       // radius-3 candidate items of a round
     int64_t c3items_cap = 0;
-    int32_t *win = nullptr;        // next-frontier window lists (2 x win_cap)
-    int64_t win_cap = 0;
     int32_t *bfs_lists = nullptr;  // per-block BFS level lists (h >= 3)
     int64_t bfs_list_len = 0;      // entries per list
     void *scan_tmp = nullptr;

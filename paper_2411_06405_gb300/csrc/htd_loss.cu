@@ -87,8 +87,6 @@ struct LossArgs {
     int32_t lost2_max;
     int32_t c3items_cap;
     int4 *c3items;
-    int32_t *win;       // next-frontier window buffers (2 x win_cap), null: not collected
-    int32_t win_cap;
     int32_t *touch2;    // h = 3: round in which the vertex last lost a radius-2 member
 };
 
@@ -119,16 +117,6 @@ __device__ __forceinline__ T vload(const T &x) {
 __device__ __forceinline__ void overflow_at(const LossArgs &a, DevStatus *st, int u) {
     if (a.h3) atomicOr(&st->halt, 1);
     else atomicMin(&st->overflow_unit, u);
-}
-
-// Supports of edges 4q .. 4q+3 (e0 = 4q) in one 16-byte load; INT_MAX past m.
-__device__ __forceinline__ int4 load_sup4(const int32_t *sup, int64_t m, int64_t e0) {
-    if (e0 + 3 < m) return *reinterpret_cast<const int4 *>(sup + e0);
-    int4 v = make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
-    if (e0 < m) v.x = sup[e0];
-    if (e0 + 1 < m) v.y = sup[e0 + 1];
-    if (e0 + 2 < m) v.z = sup[e0 + 2];
-    return v;
 }
 
 // Round kernels do nothing once the peel is over or a round halted.
@@ -221,55 +209,6 @@ __device__ __forceinline__ T warp_incl_scan(T v) {
         if (lane >= o) v += t;
     }
     return v;
-}
-
-// Hard pairs whose shorter row is long are settled by the whole warp from the two
-// alive-adjacency sets instead of a walk: a common alive neighbour exists iff the AND of
-// the two n-bit sets is non-zero.  A walk of L slots takes L dependent-ish random loads; the
-// AND takes 2W/4 coalesced 16-byte loads, so it wins once L exceeds about W/4.
-__device__ __forceinline__ void warp_dense_pairs(const LossArgs &a, int &state, int p, int q,
-                                                 unsigned &reads) {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    bool dense = false;
-    const uint32_t *ps = nullptr, *qs = nullptr;
-    if (state == kHard) {
-        const int len = min(a.row_ptr[p + 1] - a.row_ptr[p], a.row_ptr[q + 1] - a.row_ptr[q]);
-        if (4 * len > a.Wpad) {
-            unsigned r = 0;
-            ps = hub_set(a, p, r);
-            qs = hub_set(a, q, r);
-            reads += r;
-            dense = ps && qs;
-        }
-    }
-    unsigned todo = __ballot_sync(full, dense);
-    while (todo) {
-        const int l = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const uint4 *p4 = reinterpret_cast<const uint4 *>(
-            __shfl_sync(full, reinterpret_cast<unsigned long long>(ps), l));
-        const uint4 *q4 = reinterpret_cast<const uint4 *>(
-            __shfl_sync(full, reinterpret_cast<unsigned long long>(qs), l));
-        const int nv = a.Wpad >> 2;
-        bool hit = false;
-        for (int i0 = 0; i0 < nv && !hit; i0 += 4 * 32) {
-            uint4 x[4], y[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int i = i0 + 32 * j + lane;
-                x[j] = i < nv ? p4[i] : make_uint4(0, 0, 0, 0);
-                y[j] = i < nv ? q4[i] : make_uint4(0, 0, 0, 0);
-            }
-            unsigned any = 0u;
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                any |= (x[j].x & y[j].x) | (x[j].y & y[j].y) | (x[j].z & y[j].z) | (x[j].w & y[j].w);
-            hit = __any_sync(full, any != 0u);
-            reads += 32;
-        }
-        if (lane == l) state = hit ? kKept : kLost;
-    }
 }
 
 // Slots of the concatenated rows each lane loads per step of a warp's common walk (their
@@ -609,10 +548,7 @@ __device__ void ph_detect(const LossArgs &a) {
             pairs++;
             state = pair_quick(a, p, q, reads);
         }
-        if (__any_sync(0xffffffffu, state == kHard)) {
-            warp_dense_pairs(a, state, p, q, reads);
-            if (__any_sync(0xffffffffu, state == kHard)) warp_hard_pairs(a, state, p, q, reads);
-        }
+        if (__any_sync(0xffffffffu, state == kHard)) warp_hard_pairs(a, state, p, q, reads);
         record_lost_warp(a, st, state == kLost, r.x, z, u, reads);
         reads_total += reads;
     }
@@ -1096,22 +1032,6 @@ __device__ __forceinline__ void select_one(const LossArgs &a, DevStatus *st, boo
     }
 }
 
-// Selection from the last reduction's window list (every alive edge with sup <= k - 2 is
-// in it), warp-strided from `first` over `stride` threads.
-__device__ __forceinline__ void select_from_window(const LossArgs &a, DevStatus *st, int first,
-                                                   int stride) {
-    const int k = vload(st->k), round = vload(st->round), thr = k - 2;
-    const int lane = threadIdx.x & 31;
-    const int rd = vload(st->win_rd);
-    const int cnt = min(vload(st->nwin[rd]), a.win_cap);
-    const int32_t *list = a.win + (int64_t)rd * a.win_cap;
-    for (int i0 = first + (threadIdx.x & ~31); i0 < cnt; i0 += stride) {
-        const int i = i0 + lane;
-        const int e = i < cnt ? list[i] : 0;
-        select_one(a, st, i < cnt && a.sup[e] <= thr, e, k, round);
-    }
-}
-
 // Phase 1 of an incremental round: every alive edge with h-support <= k-2 joins F and is
 // removed at once (Algorithm 1, lines 7-10), and the loss detection items of its two edge
 // sides are written.  A continued round only writes the items of its remaining sides.
@@ -1123,32 +1043,21 @@ __device__ void ph_select_items(const LossArgs &a) {
     }
     const int k = vload(st->k), round = vload(st->round), thr = k - 2;
     const int lane = threadIdx.x & 31;
-    if (a.win && vload(st->win_ok)) {
-        // every candidate of this round is in the window list of the last reduction
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long *)&st->st_win_selects, 1ull);
-        select_from_window(a, st, blockIdx.x * blockDim.x, gridDim.x * blockDim.x);
-        return;
-    }
-    const int64_t stride = 16 * (int64_t)gridDim.x * blockDim.x;
-    // four 16-byte loads per thread per step (16 supports), issued before any is used
-    for (int64_t e0 = 16 * (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)); e0 < a.m;
+    const int64_t stride = 4 * (int64_t)gridDim.x * blockDim.x;
+    // four coalesced loads per thread per step, issued before any of them is used
+    for (int64_t e0 = 4 * (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)); e0 < a.m;
          e0 += stride) {
-        int sv[16];
+        int sv[4];
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const int4 v = load_sup4(a.sup, a.m, e0 + 4 * (32 * j + lane));
-            sv[4 * j] = v.x;
-            sv[4 * j + 1] = v.y;
-            sv[4 * j + 2] = v.z;
-            sv[4 * j + 3] = v.w;
+            const int64_t e = e0 + 32 * j + lane;
+            sv[j] = (e < a.m) ? a.sup[e] : INT_MAX;
         }
 #pragma unroll
-        for (int jj = 0; jj < 16; jj++) {
-            const int e = (int)(e0 + 4 * (32 * (jj >> 2) + lane) + (jj & 3));
-            select_one(a, st, sv[jj] <= thr, e, k, round);
-        }
+        for (int j = 0; j < 4; j++) select_one(a, st, sv[j] <= thr, (int)(e0 + 32 * j + lane), k, round);
     }
 }
+
 // Programmatic dependent launch: a phase kernel may be scheduled while the previous one
 // still runs; it waits here until that grid has completed and its writes are visible, then
 // lets the next phase be scheduled in turn.  (Without a programmatic launch the wait
@@ -1186,7 +1095,7 @@ __global__ void __launch_bounds__(kBlock) k_loss_apply_reduce(LossArgs a) {
     if (round_idle(a)) return;
     ph_apply(a);
     if (a.h3) ph_apply2(a);
-    minreduce_body<kBlock / 32>(a.sup, a.m, a.st, 0, a.win, a.win_cap);
+    minreduce_body<kBlock / 32>(a.sup, a.m, a.st, 0);
 }
 
 constexpr int kPBlock = 512;  // threads per block of the persistent kernel
@@ -1285,8 +1194,6 @@ LossArgs loss_args(Handle *H) {
     a.lost2_max = (int32_t)w.lost2_max;
     a.c3items_cap = (int32_t)w.c3items_cap;
     a.c3items = w.c3items;
-    a.win = w.win;
-    a.win_cap = (int32_t)w.win_cap;
     a.touch2 = w.touch2;
     return a;
 }

@@ -632,7 +632,6 @@ void free_work(PeelWork *w) {
     cudaFree(w->lost2);
     cudaFree(w->c3items);
     cudaFree(w->touch2);
-    cudaFree(w->win);
     cudaFree(w->status);
     if (w->status_host) cudaFreeHost(w->status_host);
     *w = PeelWork{};
@@ -745,8 +744,6 @@ htd_status ensure_work_impl(Handle *H, int32_t h, bool incremental, bool tiny_ta
         w.uitems_cap = 2 * w.lost_max + w.upd_budget / 32 + 1024;
         HTD_CHECK(alloc_n(&w.pitems, w.pitems_cap));
         HTD_CHECK(alloc_n(&w.uitems, w.uitems_cap));
-        w.win_cap = 1 << 16;
-        HTD_CHECK(alloc_n(&w.win, 2 * w.win_cap));
         if (h == 3) {
             // radius-2 balls (dense) with their own metadata, the round's radius-2 losses and
             // the radius-3 candidate items

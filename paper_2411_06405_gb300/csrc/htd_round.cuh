@@ -40,7 +40,7 @@ __device__ __forceinline__ void remove_edge(int e, int k, int round, const int32
 // count): round and level bookkeeping, the next level k = max(k, min + 2) (Algorithm 1's
 // bins skip empty levels), continuation of an incremental round that ran out of room, and
 // the reset of the per-round counters.
-__device__ __forceinline__ void round_finalize(DevStatus *st, int initial, bool window) {
+__device__ __forceinline__ void round_finalize(DevStatus *st, int initial) {
     __threadfence();
     const int mn = atomicAdd(&st->min_acc, 0);
     const long long al = (long long)atomicAdd((unsigned long long *)&st->alive_acc, 0ull);
@@ -65,16 +65,6 @@ __device__ __forceinline__ void round_finalize(DevStatus *st, int initial, bool 
     if (!initial) st->st_slots++;
     st->alive = al;
     if (al > 0 && !unfinished) st->k = max(st->k, mn + 2);
-    // the window list just written serves the next selection if it holds every alive edge
-    // with sup <= k - 2 (it lists sup <= win_thr, and -1 marks a list that overflowed)
-    {
-        const int w = st->win_wr;
-        st->win_ok = (window && !initial && !unfinished && st->win_thr >= 0 && st->k - 2 <= st->win_thr) ? 1 : 0;
-        st->win_rd = w;
-        st->win_wr = w ^ 1;
-        st->nwin[w ^ 1] = 0;
-        st->win_thr = st->k - 2 + kWindow;
-    }
     st->min_acc = INT_MAX;
     st->alive_acc = 0;
     st->done_blocks = 0u;
@@ -95,66 +85,28 @@ __device__ __forceinline__ void round_finalize(DevStatus *st, int initial, bool 
 
 // Minimum alive support and alive count over all edges; the last block to finish closes the
 // round.  Every thread of every block calls it; `NW` = warps per block.
-// win (nullable): the window buffers (2 x win_cap entries); every alive edge with sup <=
-// st->win_thr is appended to buffer st->win_wr; an overflow sets win_thr to -1.
-// Returns true in the block that closed the round.
 template <int NW>
-__device__ __forceinline__ bool minreduce_body(const int32_t *__restrict__ sup, int64_t m,
-                                               DevStatus *st, int initial,
-                                               int32_t *win = nullptr, int32_t win_cap = 0) {
+__device__ __forceinline__ void minreduce_body(const int32_t *__restrict__ sup, int64_t m,
+                                               DevStatus *st, int initial) {
     __shared__ int32_t s_min[NW];
     __shared__ long long s_cnt[NW];
     __shared__ bool s_last;
     int lmin = INT_MAX;
     long long lc = 0;
-    // four 16-byte loads per thread per step (16 supports), issued before any is used
-    const int64_t stride = 16 * (int64_t)gridDim.x * blockDim.x;
-    // block-uniform trip count (the window's warp ballots need every lane)
-    for (int64_t b0 = 16 * (blockIdx.x * (int64_t)blockDim.x); b0 < m; b0 += stride) {
-        const int64_t e0 = b0 + 4 * threadIdx.x;
-        int4 v[4];
+    // four coalesced loads per thread per step, issued before any of them is used
+    const int64_t stride = 4 * (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = 4 * (blockIdx.x * (int64_t)blockDim.x) + threadIdx.x; e0 < m; e0 += stride) {
+        int sv[4];
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const int64_t e = e0 + 4 * (int64_t)j * blockDim.x;
-            if (e + 3 < m) {
-                v[j] = *reinterpret_cast<const int4 *>(sup + e);
-            } else {
-                v[j] = make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
-                if (e < m) v[j].x = sup[e];
-                if (e + 1 < m) v[j].y = sup[e + 1];
-                if (e + 2 < m) v[j].z = sup[e + 2];
-            }
+            const int64_t e = e0 + (int64_t)j * blockDim.x;
+            sv[j] = (e < m) ? sup[e] : INT_MAX;
         }
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const int sv[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                if (sv[c] != INT_MAX) {
-                    lmin = min(lmin, sv[c]);
-                    lc++;
-                }
-            }
-            if (win) {
-                // window candidates of this quad, one atomic per warp
-                const int thr = *(volatile int32_t *)&st->win_thr;
-                const int64_t e = e0 + 4 * (int64_t)j * blockDim.x;
-#pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    const bool p = sv[c] <= thr;  // removed edges hold INT_MAX
-                    const unsigned bal = __ballot_sync(0xffffffffu, p);
-                    if (bal == 0u) continue;
-                    const int lane = threadIdx.x & 31;
-                    const int wb = *(volatile int32_t *)&st->win_wr;
-                    int base = 0;
-                    if (lane == __ffs(bal) - 1) base = atomicAdd(&st->nwin[wb], __popc(bal));
-                    base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
-                    const int pos = base + __popc(bal & lanemask_lt());
-                    if (p) {
-                        if (pos < win_cap) win[(int64_t)wb * win_cap + pos] = (int32_t)(e + c);
-                        else atomicExch(&st->win_thr, -1);
-                    }
-                }
+            if (sv[j] != INT_MAX) {
+                lmin = min(lmin, sv[j]);
+                lc++;
             }
         }
     }
@@ -180,9 +132,8 @@ __device__ __forceinline__ bool minreduce_body(const int32_t *__restrict__ sup, 
         s_last = (ticket == gridDim.x - 1);
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) round_finalize(st, initial, win != nullptr);
+    if (s_last && threadIdx.x == 0) round_finalize(st, initial);
     __syncthreads();
-    return s_last;
 }
 
 // Barrier across all blocks of a cooperative launch (all co-resident, at most 64 x 32

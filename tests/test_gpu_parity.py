@@ -245,8 +245,6 @@ def test_graph_and_direct_launch_agree_and_repeat(htd, oracle_mod):
     assert 0 < s3["timed_slots"] <= s3["slots"] and s3["ms_find"] > 0 and s3["slots"] >= s3["rounds"]
     assert 0 < s5["timed_slots"] <= s5["slots"] and s5["ms_ball"] > 0
     assert s1["incremental"] == 1 and s5["incremental"] == 0
-    # most rounds stay on their level: their frontier comes from the reduction's window list
-    assert 0 < s1["window_selects"] < s1["rounds"] and s5["window_selects"] == 0
     # changing h on the same handle and coming back
     t_h3, _, _ = htd.htd_truss_decompose(g, 3)
     t4, _, _ = htd.htd_truss_decompose(g, 2)
