@@ -38,6 +38,7 @@ CANDIDATES = [
     {"max_union_vertices": 1 << 16, "flags": _lib.HTD_OPT_REBUILD},
 ]
 DEFAULT = {"max_union_vertices": 1 << 18, "flags": 0}
+BLOCK_MAX_NCLASS = 9  # log2 class of n above which one block per graph is not tried
 
 
 def group_key(n: int, src, dst, h: int) -> str:
@@ -82,8 +83,13 @@ def tune(graphs, sample: int = 64, candidates=None, seed: int = 0):
     table = {}
     for key, gs in sorted(groups.items()):
         pick = gs if len(gs) <= sample else [gs[i] for i in rng.choice(len(gs), sample, replace=False)]
+        nclass = int(key.split("_")[1][1:])
         times = {}
         for ci, c in enumerate(cands):
+            # one block per graph only pays for graphs of up to about a thousand vertices
+            # (a block's rounds grow with n^2 / 32 words); larger groups skip that candidate
+            if c["flags"] & _lib.HTD_OPT_BATCH_BLOCKS and nclass > BLOCK_MAX_NCLASS:
+                continue
             times[ci] = _time_batch(htd, torch, pick, c)
         best = min(times, key=times.get)
         table[key] = dict(cands[best], ms=times, sample=len(pick))
