@@ -495,6 +495,34 @@ def measure_hindex(htd, torch, name: str, h: int, sweeps_list=(1, 8)):
     return out
 
 
+def ball_study(htd, torch):
+    """Ball representation and hop threshold study: the same graphs decomposed with every
+    ball dense (n-bit rows, one load per membership test) and in the compact form (sorted
+    (word index, word) pairs; h = 3 then peels by rebuilds), and at h = 4 (rebuild rounds);
+    device time and the ball storage of each."""
+    out = []
+    for name, h in (("rmat_s16", 2), ("dcsbm_n50k", 2), ("dcsbm_n50k", 3), ("dcsbm_n50k", 4),
+                    ("er_n2000", 4), ("rmat_s16", 1)):
+        spec = config_graph(name)
+        src = torch.from_numpy(spec.src).cuda()
+        dst = torch.from_numpy(spec.dst).cuda()
+        for label, flags in (("dense", 0), ("compact", htd.HTD_OPT_COMPACT_BALLS)):
+            if h >= 4 and label == "compact":
+                continue  # h >= 4 always stores the smaller form
+            g = htd.htd_build_csr(spec.n, src, dst)
+            htd.htd_truss_decompose(g, h, flags=flags)  # warm (graph capture, allocation)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            _, _, st = htd.htd_truss_decompose(g, h, flags=flags)
+            e.record()
+            torch.cuda.synchronize()
+            out.append({"graph": name, "n": spec.n, "m": g.m, "h": h, "balls": label,
+                        "incremental": st["incremental"], "ms": a.elapsed_time(e),
+                        "rounds": st["rounds"], "ball_pool_bytes": st["ball_pool_bytes"]})
+            g.free()
+    return out
+
+
 def host_np(t):
     return t.cpu().numpy() if t is not None else None
 
@@ -643,8 +671,21 @@ def main():
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream entry")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched entry")
     ap.add_argument("--no-hindex", action="store_true", help="skip the H-index engine entries")
+    ap.add_argument("--study", action="store_true",
+                    help="ball representation / hop threshold study instead of the bench line")
     args = ap.parse_args()
     world, rank, local = dist_env()
+    if args.study:
+        import torch
+
+        import paper_2411_06405_gb300 as htd
+        from paper_2411_06405_gb300 import build as cuda_build
+
+        torch.cuda.set_device(local)
+        cuda_build.build()
+        htd._lib.load()
+        print(json.dumps({"study": "balls_and_h", "rows": ball_study(htd, torch)}), flush=True)
+        return
     if world > 1:
         import torch
 
