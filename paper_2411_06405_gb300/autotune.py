@@ -15,8 +15,10 @@ out, and the best setting depends on the graphs:
 Graphs are grouped by a key of (h, log2 class of n, log2 class of the largest degree).
 ``tune`` times every candidate on a sample of each group (CUDA events, after a warm-up) and
 keeps the fastest; the resulting table is JSON, keyed by group.  ``decompose`` runs a batch
-with a table: each group with its own setting, results returned in input order.  The results
-do not depend on the setting (every candidate is an exact decomposition), only the time.
+with a table in two calls: the graphs whose group chose one block per graph, and all the
+others as unions (peeled concurrently inside the call) with the setting most of their edges'
+groups chose; results come back in input order.  The results do not depend on the setting
+(every candidate is an exact decomposition), only the time.
 """
 
 from __future__ import annotations
@@ -106,37 +108,53 @@ def load(path: str):
         return json.load(f)
 
 
-def decompose(graphs, table=None, device=None):
-    """Decomposes a batch with the table's setting for each group (DEFAULT for groups the
-    table lacks); returns (list of int32 CUDA tensors in input order, {setting: graphs})."""
-    import paper_2411_06405_gb300 as htd
-
+def _partition(graphs, table):
+    """Graph indices by the setting the batch runs them with.  Graphs whose group chose one
+    block per graph form one block-per-graph call; all others form one union call (their
+    unions run concurrently inside it), with the union size and round variant that most of
+    their edges' groups chose."""
     table = table or {}
-    parts = defaultdict(list)
+    blocks, rest = [], []
+    votes = defaultdict(int)
     for i, g in enumerate(graphs):
         ent = table.get(group_key(*g), DEFAULT)
-        parts[(int(ent["max_union_vertices"]), int(ent["flags"]))].append(i)
+        if int(ent["flags"]) & _lib.HTD_OPT_BATCH_BLOCKS:
+            blocks.append(i)
+        else:
+            rest.append(i)
+            votes[(int(ent["max_union_vertices"]), int(ent["flags"]))] += int(np.asarray(g[1]).size)
+    cap, flags = max(votes, key=votes.get) if votes else (DEFAULT["max_union_vertices"], DEFAULT["flags"])
+    parts = []
+    if blocks:
+        parts.append((blocks, 1 << 18, _lib.HTD_OPT_BATCH_BLOCKS))
+    if rest:
+        parts.append((rest, cap, flags))
+    return parts
+
+
+def decompose(graphs, table=None, device=None):
+    """Decomposes a batch with the table's settings (see _partition); returns (list of int32
+    CUDA tensors in input order, {setting: graphs})."""
+    import paper_2411_06405_gb300 as htd
+
     out = [None] * len(graphs)
-    for (cap, flags), idx in sorted(parts.items()):
+    summary = {}
+    for idx, cap, flags in _partition(graphs, table):
         res, _ = htd.htd_truss_decompose_batched([graphs[i] for i in idx], flags=flags,
                                                  max_union_vertices=cap, device=device)
         for i, r in zip(idx, res):
             out[i] = r
-    return out, {f"{cap}/{flags}": len(idx) for (cap, flags), idx in parts.items()}
+        summary[f"{cap}/{flags}"] = len(idx)
+    return out, summary
 
 
 def prepare(graphs, table=None, device=None):
-    """Splits a batch by the table's settings and puts each part on the device once:
-    returns a list of (BatchInput, input indices, max_union_vertices, flags)."""
+    """The partition of a batch put on the device once: a list of (BatchInput, input
+    indices, max_union_vertices, flags)."""
     import paper_2411_06405_gb300 as htd
 
-    table = table or {}
-    parts = defaultdict(list)
-    for i, g in enumerate(graphs):
-        ent = table.get(group_key(*g), DEFAULT)
-        parts[(int(ent["max_union_vertices"]), int(ent["flags"]))].append(i)
     return [(htd.BatchInput([graphs[i] for i in idx], device), idx, cap, flags)
-            for (cap, flags), idx in sorted(parts.items())]
+            for idx, cap, flags in _partition(graphs, table)]
 
 
 def run_prepared(prepared, count: int):
