@@ -190,7 +190,12 @@ htd_status htd_truss_decompose_host(int32_t n, const int32_t *src_host,
  * decompositions (h-support counts only vertices of the edge's own component), so the
  * graphs of each h are packed, in input order, into disjoint unions of at most
  * max_union_vertices vertices and each union is peeled once (htd_truss_decompose_ex with
- * `flags`).  Results are identical to decomposing each graph alone.
+ * `flags`).  The unions are independent and are peeled concurrently by up to 8 worker
+ * threads, each on its own stream, as many at once as their footprint estimates fit 70% of
+ * the free device memory (a union that still runs out of memory is retried alone).  With
+ * HTD_OPT_BATCH_BLOCKS the graphs of at most 8,192 vertices and h <= 3 are instead peeled
+ * one block per graph in a single persistent launch.  Results are identical to decomposing
+ * each graph alone.
  *   num_graphs        number of graphs (>= 0).
  *   n, h              host arrays of num_graphs: vertex count (0 <= n <= HTD_MAX_N) and hop
  *                     threshold (1 <= h <= HTD_MAX_H) of each graph.
