@@ -66,8 +66,6 @@ struct DevStatus {
     int64_t st_c3_pairs;       // radius-3 candidate pairs tested
     int64_t st_lost2;          // radius-2 lost pairs
     int64_t st_recovered;      // rounds finished by the rebuild recovery
-    int32_t q_c3;              // next radius-3 candidate item to test (work queue)
-    int32_t pad3;
 };
 
 

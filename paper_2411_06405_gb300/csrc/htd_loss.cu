@@ -901,12 +901,8 @@ __device__ void ph_test3(const LossArgs &a) {
     const int round = vload(st->round);
     const int lane = threadIdx.x & 31;
     unsigned long long pairs = 0ull, reads_total = 0ull;
-    // items differ widely in cost: each warp takes the next one from a shared counter
-    for (;;) {
-        int it = 0;
-        if (lane == 0) it = atomicAdd(&st->q_c3, 1);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= nitems) break;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nwarps) {
         const int4 item = a.c3items[it];
         const int x = item.x, y = item.y;
         unsigned reads = 0;

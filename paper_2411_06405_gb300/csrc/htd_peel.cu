@@ -998,7 +998,6 @@ __global__ void k_recover_reset(DevStatus *st) {
     st->npitems = 0;
     st->nuitems = 0;
     st->nc3items = 0;
-    st->q_c3 = 0;
     st->upd_work = 0;
     st->overflow_unit = INT_MAX;
     for (int j = 0; j < kMaxH; j++) st->cand_cnt[j] = 0;
