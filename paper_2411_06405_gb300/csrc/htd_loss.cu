@@ -211,6 +211,67 @@ __device__ __forceinline__ T warp_incl_scan(T v) {
     return v;
 }
 
+// Slots of the concatenated rows each lane loads per step of a warp's common walk (their
+// loads are independent, so a step costs two round trips whatever the count).
+constexpr int kWalkUnroll = 4;
+
+// Common alive neighbours for the warp's hard pairs (lanes with state == kHard; p the
+// shorter row), all at once: the pairs' rows of p are laid end to end and the warp walks
+// the concatenation 32 x kWalkUnroll slots per step, each lane finding the pair its slot belongs to by a
+// binary search over the lanes' running row lengths.  A pair is kept at its first alive
+// neighbour that q also has; the walk skips kept pairs and stops once none is pending.
+// Called by whole warps.
+__device__ __forceinline__ void warp_hard_pairs(const LossArgs &a, int &state, int p, int q,
+                                                unsigned &reads) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool hard = state == kHard;
+    int rb = 0, len = 0;
+    const uint32_t *qset = nullptr;
+    if (hard) {
+        rb = a.row_ptr[p];
+        len = a.row_ptr[p + 1] - rb;
+        qset = hub_set(a, q, reads);
+        reads += 2;
+    }
+    const int incl = warp_incl_scan(len);
+    const int excl = incl - len;
+    const int total = __shfl_sync(full, incl, 31);
+    unsigned pending = __ballot_sync(full, hard);
+    unsigned kept = 0u;
+    for (int base = 0; base < total && pending; base += 32 * kWalkUnroll) {
+        int y[kWalkUnroll], own[kWalkUnroll];
+#pragma unroll
+        for (int j = 0; j < kWalkUnroll; j++) {
+            const int idx = base + 32 * j + lane;
+            // owner lane: the number of lanes whose rows end at or before idx
+            int o = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(full, incl, o + step - 1) <= idx) o += step;
+            o = min(o, 31);
+            const int ex = __shfl_sync(full, excl, o), rbo = __shfl_sync(full, rb, o);
+            own[j] = o;
+            y[j] = (idx < total && ((pending >> o) & 1u)) ? a.col_live[rbo + idx - ex] : -1;
+        }
+        unsigned hits = 0u;
+#pragma unroll
+        for (int j = 0; j < kWalkUnroll; j++) {
+            const int qo = __shfl_sync(full, q, own[j]);
+            const uint32_t *qs = reinterpret_cast<const uint32_t *>(
+                __shfl_sync(full, reinterpret_cast<unsigned long long>(qset), own[j]));
+            if (y[j] >= 0) {
+                reads++;
+                if (alive_adjacent_set(a, qs, qo, y[j], reads)) hits |= 1u << own[j];
+            }
+        }
+        hits = __reduce_or_sync(full, hits);
+        kept |= hits;
+        pending &= ~hits;
+    }
+    if (hard) state = ((kept >> lane) & 1u) ? kKept : kLost;
+}
+
 // Is w in the stored ball of z (dense words, or sorted (word index, word) pairs)?
 // `bytes` counts the algorithmic bytes: 8 of metadata plus the words probed.
 __device__ __forceinline__ bool ball_contains_meta(const LossArgs &a, int2 meta, int w,
@@ -445,21 +506,10 @@ __device__ void ph_pair_items(const LossArgs &a) {
 }
 
 // Loss detection, one warp per item: lane i tests the pair of slot item.y + i.  A pair is
-// kept if its endpoints are adjacent or (h = 2) share an alive neighbour.  The pairs whose
-// test needs a longer row scan are walked by the whole block: the rows of the block's hard
-// pairs (up to 256, from its 8 items) are laid end to end and 1,024 slots are tested per
-// step, each thread finding its pair by a binary search over the running row lengths, so a
-// single item with long rows gets the block's eight warps rather than one.  The walk stops
-// once every hard pair of the block has found a common neighbour.
-template <int BS>
+// kept if its endpoints are adjacent or (h = 2) share an alive neighbour; the pairs whose
+// test needs a longer row scan are walked by the whole warp together.
 __device__ void ph_detect(const LossArgs &a) {
-    constexpr int NW = BS / 32;
     __shared__ unsigned long long s_pairs, s_reads;
-    __shared__ int s_len[BS], s_incl[BS], s_rb[BS], s_q[BS];
-    __shared__ unsigned long long s_qs[BS];
-    __shared__ unsigned s_hard[NW], s_kept[NW];
-    __shared__ int s_scan[NW];
-    __shared__ int s_more;
     DevStatus *st = a.st;
     if (threadIdx.x == 0) {
         s_pairs = 0ull;
@@ -467,105 +517,40 @@ __device__ void ph_detect(const LossArgs &a) {
     }
     __syncthreads();
     const int nitems = min(vload(st->npitems), a.pitems_cap), round = vload(st->round);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     unsigned long long pairs = 0ull, reads_total = 0ull;
-    // block-uniform trip count: the block's barriers need every thread
-    for (int base = blockIdx.x * NW; base < nitems; base += gridDim.x * NW) {
-        const int it = base + wid;
-        int u = -1, x = 0, z = -1;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nwarps) {
+        const int4 item = a.pitems[it];
+        const int u = item.x;
+        // sides past an overflow are redone by the next slot of the round: skip them now
+        if (u < 0 || u > *(volatile int *)&st->overflow_unit) continue;
+        UnitInfo r;
+        r.x = item.z;
+        r.y = item.w;
+        r.rb = a.row_ptr[r.y];
+        r.stop = (a.h < 2) ? r.rb : a.row_ptr[r.y + 1];
+        const int sl = item.y + lane;
+        int z = -1;
         unsigned reads = 0;
-        if (it < nitems) {
-            const int4 item = a.pitems[it];
-            // sides past an overflow are redone by the next slot of the round: skip them now
-            if (item.x >= 0 && item.x <= *(volatile int *)&st->overflow_unit) {
-                u = item.x;
-                x = item.z;
-                const int y = item.w;
-                const int rb = a.row_ptr[y];
-                const int stop = (a.h < 2) ? rb : a.row_ptr[y + 1];
-                const int sl = item.y + lane;
-                if (sl < stop) {
-                    if (sl < rb) {
-                        z = y;
-                    } else {
-                        // an old neighbour: alive, or removed in this round
-                        const int c = a.col[sl], cl = a.col_live[sl];
-                        reads += 2;
-                        if (c != x && (cl >= 0 || cl == -(round + 1))) z = c;
-                    }
-                }
+        if (sl < r.stop) {
+            if (sl < r.rb) {
+                z = r.y;
+            } else {
+                // an old neighbour: alive, or removed in this round
+                const int c = a.col[sl], cl = a.col_live[sl];
+                reads += 2;
+                if (c != r.x && (cl >= 0 || cl == -(round + 1))) z = c;
             }
         }
-        int state = kKept, p = x, q = z;
+        int state = kKept, p = r.x, q = z;
         if (z >= 0) {
             pairs++;
             state = pair_quick(a, p, q, reads);
         }
-        // the hard pairs' rows of p (the shorter row), laid end to end over the block
-        int len = 0, rbp = 0;
-        unsigned long long qs = 0ull;
-        if (state == kHard) {
-            rbp = a.row_ptr[p];
-            len = a.row_ptr[p + 1] - rbp;
-            qs = reinterpret_cast<unsigned long long>(hub_set(a, q, reads));
-            reads += 2;
-        }
-        int total;
-        const int excl = block_exclusive_scan<BS, int>(len, &total, s_scan);
-        s_len[threadIdx.x] = len;
-        s_incl[threadIdx.x] = excl + len;
-        s_rb[threadIdx.x] = rbp;
-        s_q[threadIdx.x] = q;
-        s_qs[threadIdx.x] = qs;
-        const unsigned hb = __ballot_sync(0xffffffffu, state == kHard);
-        if (lane == 0) {
-            s_hard[wid] = hb;
-            s_kept[wid] = 0u;
-        }
-        __syncthreads();
-        for (int off = 0; off < total; off += 4 * BS) {
-            int yv[4], own[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int idx = off + j * BS + threadIdx.x;
-                yv[j] = -1;
-                own[j] = 0;
-                if (idx < total) {
-                    // owner: the first pair whose running length passes idx
-                    int lo = 0, hi = BS - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (s_incl[mid] > idx) hi = mid;
-                        else lo = mid + 1;
-                    }
-                    own[j] = lo;
-                    if (!((s_kept[lo >> 5] >> (lo & 31)) & 1u))
-                        yv[j] = a.col_live[s_rb[lo] + idx - (s_incl[lo] - s_len[lo])];
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                if (yv[j] >= 0) {
-                    const int o = own[j];
-                    reads++;
-                    const uint32_t *qset = reinterpret_cast<const uint32_t *>(s_qs[o]);
-                    if (alive_adjacent_set(a, qset, s_q[o], yv[j], reads))
-                        atomicOr(&s_kept[o >> 5], 1u << (o & 31));
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int more = 0;
-                for (int w = 0; w < NW; w++) more |= (s_hard[w] & ~s_kept[w]) != 0u;
-                s_more = more;
-            }
-            __syncthreads();
-            if (!s_more) break;
-        }
-        if (state == kHard) state = ((s_kept[wid] >> lane) & 1u) ? kKept : kLost;
-        record_lost_warp(a, st, state == kLost, x, z, u, reads);
+        if (__any_sync(0xffffffffu, state == kHard)) warp_hard_pairs(a, state, p, q, reads);
+        record_lost_warp(a, st, state == kLost, r.x, z, u, reads);
         reads_total += reads;
-        __syncthreads();  // the shared rows are rewritten by the next items
     }
     for (int o = 16; o > 0; o >>= 1) {
         pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
@@ -820,8 +805,7 @@ __device__ void ph_c3_items(const LossArgs &a) {
 // Common walk of the warp's hard radius-3 pairs (lanes with state == kHard): w is the
 // endpoint whose alive row is walked, t the other one; the pair is kept at the first alive
 // neighbour y of w with t in B2_new(y).  The rows are laid end to end and walked 128 slots
-// per step, each lane finding its pair by a binary search over the lanes' running row
-// lengths.  Called by whole warps.
+// per step as in warp_hard_pairs.  Called by whole warps.
 __device__ __forceinline__ void warp_walk3(const LossArgs &a, int &state, int w, int t, int round,
                                            unsigned &reads) {
     const unsigned full = 0xffffffffu;
@@ -1093,7 +1077,7 @@ __global__ void __launch_bounds__(kBlock) k_inc_select(LossArgs a) {
 __global__ void __launch_bounds__(kBlock) k_loss_detect(LossArgs a) {
     phase_entry();
     if (round_idle(a)) return;
-    ph_detect<kBlock>(a);
+    ph_detect(a);
     if (a.h3) ph_c3_items(a);
 }
 __global__ void __launch_bounds__(kBlock) k_loss3_test(LossArgs a) {
@@ -1143,7 +1127,7 @@ __global__ void __launch_bounds__(kPBlock, 3) k_rounds_persistent(LossArgs a, in
         if (vload(st->alive) == 0 || vload(st->err) != 0) break;
         ph_select_items(a);
         if (!phase_done(0)) return;
-        ph_detect<kPBlock>(a);
+        ph_detect(a);
         if (!phase_done(1)) return;
         ph_delta(a);
         if (!phase_done(2)) return;
