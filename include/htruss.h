@@ -99,6 +99,7 @@ typedef struct htd_stats {
     int64_t pairs2_lost;     /* incremental h = 3 rounds: pairs that left radius-2 balls */
     int64_t rounds_rebuilt;  /* incremental h = 3 rounds that ran out of room and were
                                 finished by rebuilding the candidates' balls */
+    double alg_bytes_hsup_initial; /* the part of alg_bytes_hsup taken by the initial pass */
 } htd_stats;
 
 /* Option flags for htd_truss_decompose_ex. */

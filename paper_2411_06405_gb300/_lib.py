@@ -74,6 +74,7 @@ class HtdStats(ctypes.Structure):
         ("pairs3_tested", ctypes.c_int64),
         ("pairs2_lost", ctypes.c_int64),
         ("rounds_rebuilt", ctypes.c_int64),
+        ("alg_bytes_hsup_initial", ctypes.c_double),
     ]
 
     def as_dict(self):

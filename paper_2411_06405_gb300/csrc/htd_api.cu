@@ -533,6 +533,7 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
         local.frontier_edges = s->st_frontier;
         local.alg_bytes_ball = (double)s->st_bytes_ball;
         local.alg_bytes_hsup = (double)s->st_bytes_hsup;
+        local.alg_bytes_hsup_initial = (double)s->st_bytes_hsup_init;
         local.alg_bytes_detect = (double)s->st_bytes_detect;
         local.alg_bytes_update = (double)s->st_bytes_update;
         local.kernel_launches = launches;

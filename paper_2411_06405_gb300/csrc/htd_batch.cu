@@ -85,6 +85,7 @@ void add_stats(htd_stats *acc, const htd_stats &s) {
     acc->timed_slots += s.timed_slots;
     acc->alg_bytes_ball += s.alg_bytes_ball;
     acc->alg_bytes_hsup += s.alg_bytes_hsup;
+    acc->alg_bytes_hsup_initial += s.alg_bytes_hsup_initial;
     acc->alg_bytes_detect += s.alg_bytes_detect;
     acc->alg_bytes_update += s.alg_bytes_update;
     acc->ms_initial_ball += s.ms_initial_ball;

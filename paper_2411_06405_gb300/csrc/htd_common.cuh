@@ -38,6 +38,7 @@ struct DevStatus {
     int64_t st_recomputed;     // h-support recomputations (after the initial pass)
     unsigned long long st_bytes_ball;  // algorithmic bytes, ball builds
     unsigned long long st_bytes_hsup;  // algorithmic bytes, intersections
+    unsigned long long st_bytes_hsup_init;  // the initial pass's share of st_bytes_hsup
     // incremental (h <= 2) rounds
     int32_t nlost;             // lost-pair records of the current batch (duplicates nulled)
     int32_t cont;              // 1: the current round continues (its frontier is removed)

@@ -381,7 +381,10 @@ __global__ void __launch_bounds__(kBlock) k_hsup(HsupArgs a) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (a.count_bytes && s_bytes) atomicAdd(&st->st_bytes_hsup, s_bytes);
+        if (a.count_bytes && s_bytes) {
+            atomicAdd(&st->st_bytes_hsup, s_bytes);
+            if (a.initial) atomicAdd(&st->st_bytes_hsup_init, s_bytes);
+        }
         if (!a.initial && s_owned) atomicAdd((unsigned long long *)&st->st_recomputed,
                                              (unsigned long long)s_owned);
     }
