@@ -238,12 +238,7 @@ def _phase_classes(st, h):
     if st["incremental"] and h == 3:
         return [("k_inc_select", st["ms_select"] / timed),
                 ("k_loss_detect (radius 2, radius-3 items)", st["ms_remove"] / timed),
-                ("k_loss3_test + k_loss_walk", st["ms_find"] / timed),
-                ("k_loss_delta", st["ms_update"] / timed),
-                ("k_loss_apply_reduce", st["ms_minreduce"] / timed)]
-    if st["incremental"] and h >= 2:
-        return [("k_inc_select", st["ms_select"] / timed),
-                ("k_loss_detect + k_loss_walk", st["ms_find"] / timed),
+                ("k_loss3_test", st["ms_find"] / timed),
                 ("k_loss_delta", st["ms_update"] / timed),
                 ("k_loss_apply_reduce", st["ms_minreduce"] / timed)]
     if st["incremental"]:
@@ -342,13 +337,12 @@ def measure_workload(htd, torch, lib, name, h, steps, warmup, flush, stream, dev
     if stp["incremental"] and h == 3:
         phases["k_inc_select"]["alg_bytes_host"] = hb["select"]
         phases["k_loss_detect (radius 2, radius-3 items)"]["alg_bytes_host"] = hb["detect"]
-        phases["k_loss3_test + k_loss_walk"]["alg_bytes_kernel"] = stp["alg_bytes_detect"]
+        phases["k_loss3_test"]["alg_bytes_kernel"] = stp["alg_bytes_detect"]
         phases["k_loss_delta"]["alg_bytes_kernel"] = stp["alg_bytes_update"]
     elif stp["incremental"]:
-        det = "k_loss_detect + k_loss_walk" if h >= 2 else "k_loss_detect"
         phases["k_inc_select"]["alg_bytes_host"] = hb["select"]
-        phases[det]["alg_bytes_host"] = hb["detect"]
-        phases[det]["alg_bytes_kernel"] = stp["alg_bytes_detect"]
+        phases["k_loss_detect"]["alg_bytes_host"] = hb["detect"]
+        phases["k_loss_detect"]["alg_bytes_kernel"] = stp["alg_bytes_detect"]
         phases["k_loss_delta"]["alg_bytes_kernel"] = stp["alg_bytes_update"]
     else:
         phases["k_select"]["alg_bytes_host"] = hb["select"]

@@ -332,7 +332,7 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
     API_CHECK(cudaStreamSynchronize(H->pstream));
     API_TRY(check_status_err(w.status_host));
 
-    const int per_round = w.inc3 ? 6 : incremental ? (h >= 2 ? 5 : 4) : h + 6;
+    const int per_round = w.inc3 ? 5 : incremental ? 4 : h + 6;
     const bool persistent = incremental && h <= 2 && (flags & HTD_OPT_PERSISTENT_ROUNDS) != 0;
     if (persistent && w.status_host->alive > 0) {
         // one cooperative launch runs up to kPersistentSlots round slots; the host checks the

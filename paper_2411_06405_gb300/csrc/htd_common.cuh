@@ -67,8 +67,6 @@ struct DevStatus {
     int64_t st_c3_pairs;       // radius-3 candidate pairs tested
     int64_t st_lost2;          // radius-2 lost pairs
     int64_t st_recovered;      // rounds finished by the rebuild recovery
-    int32_t ndpairs;           // long walks handed to k_loss_walk in the current batch
-    int32_t ndchunks;          // their 128-slot chunks
 };
 
 

@@ -85,12 +85,6 @@ struct PeelWork {
     int32_t *touch2 = nullptr;     // n: round in which the vertex last lost a radius-2 member
     int4 *c3items = nullptr;       // radius-3 candidate items of a round
     int64_t c3items_cap = 0;
-    // long common walks of the loss tests, finished in 128-slot chunks by k_loss_walk
-    int4 *dpairs = nullptr;        // two int4 per pair: (w, t, x, z), (unit, 2 chunks + kind, row start, row length)
-    int32_t *dflag = nullptr;      // two int32 per pair: hit, chunks done (zero between launches)
-    int2 *dchunks = nullptr;       // (pair, first slot offset in w's row); pair < 0: unused
-    int64_t dpairs_cap = 0;
-    int64_t dchunks_cap = 0;
     int32_t *bfs_lists = nullptr;  // per-block BFS level lists (h >= 3)
     int64_t bfs_list_len = 0;      // entries per list
     void *scan_tmp = nullptr;
@@ -171,7 +165,7 @@ htd_status batch_block_run(const std::vector<BlockGraphDescHost> &graphs, cudaSt
 htd_status hindex_run(htd_graph *G, Handle *H, int32_t h, int32_t sweeps, int32_t max_iter,
                       int32_t *truss_dev, int32_t *hval_dev, htd_hindex_stats *stats, cudaStream_t s);
 
-// One incremental round (h <= 3) as five launches (h = 1: four; h = 3: six), the graph path (htd_loss.cu).
+// One incremental round (h <= 3) as four (h = 3: five) launches, the graph path (htd_loss.cu).
 htd_status enqueue_incremental_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t *evs,
                                      unsigned record_flags);
 

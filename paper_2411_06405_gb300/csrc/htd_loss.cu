@@ -22,11 +22,6 @@
 // that batch), and a pair whose stored bit is already clear was handled by an earlier
 // batch of the same round, so it is skipped.  Detection records the first frontier edge
 // side it could not finish; the next round slot resumes there without selecting anew.
-//
-// A common-neighbour walk over a long row would hold up its whole launch: after 256 slots
-// the rest of an undecided row is split into 128-slot chunks that a separate launch
-// (k_loss_walk) spreads over every warp of the GPU; the warp that finishes a pair's last
-// chunk decides and records the pair.
 #include <algorithm>
 #include <cstdint>
 
@@ -93,14 +88,6 @@ struct LossArgs {
     int32_t c3items_cap;
     int4 *c3items;
     int32_t *touch2;    // h = 3: round in which the vertex last lost a radius-2 member
-    // long common walks: a pair still undecided after defer_min slots of its row hands the
-    // rest of the row to k_loss_walk in 128-slot chunks (0: every walk stays in its warp)
-    int32_t defer_min;
-    int32_t dpairs_cap;
-    int32_t dchunks_cap;
-    int4 *dpairs;       // two int4 per pair: (w, t, x, z), (unit, 2 chunks + kind, row start, row length)
-    int32_t *dflag;     // two int32 per pair: hit, chunks done
-    int2 *dchunks;      // (pair, first slot offset in w's row); pair < 0: unused entry
 };
 
 __device__ __forceinline__ unsigned long long pair_key(int p, int q) {
@@ -170,6 +157,10 @@ __device__ __forceinline__ bool alive_adjacent_set(const LossArgs &a, const uint
     return false;
 }
 
+__device__ __forceinline__ bool alive_adjacent(const LossArgs &a, int p, int q, unsigned &reads) {
+    return alive_adjacent_set(a, hub_set(a, p, reads), p, q, reads);
+}
+
 // Short rows are scanned by one lane; pairs whose shorter row is longer go to the warp.
 constexpr int kInlineScan = 8;
 
@@ -224,145 +215,14 @@ __device__ __forceinline__ T warp_incl_scan(T v) {
 // loads are independent, so a step costs two round trips whatever the count).
 constexpr int kWalkUnroll = 4;
 
-// Is the pair {p,q} among this round's radius-2 losses?
-__device__ __forceinline__ bool lost2_now(const LossArgs &a, int p, int q, unsigned &bytes) {
-    const unsigned long long key = pair_key(p, q);
-    unsigned long long slot = mix64(key) & a.cap2_mask;
-    for (unsigned long long probe = 0; probe <= a.cap2_mask; probe++) {
-        const unsigned long long k = a.keys2[slot];
-        bytes += 8;
-        if (k == key) return true;
-        if (k == kEmpty) return false;
-        slot = (slot + 1) & a.cap2_mask;
-    }
-    return false;
-}
-
-// q in B2_new(z): the stored radius-2 bit, unless this round lost the pair (the pair set is
-// probed only for vertices that lost a radius-2 member this round).
-__device__ __forceinline__ bool in_b2_new(const LossArgs &a, int z, int q, int round, unsigned &bytes) {
-    bytes += 4;
-    if (!((a.pool2[(int64_t)z * a.Wpad + (q >> 5)] >> (q & 31)) & 1u)) return false;
-    if (z == q) return true;
-    bytes += 4;
-    if (a.touch2[z] != round) return true;
-    return !lost2_now(a, z, q, bytes);
-}
-
-// Common walk of the warp's undecided pairs: every lane with `want` walks slots
-// [rb + from, rb + to) of its row w, and a lane's pair is kept at the first alive neighbour
-// y of w that passes its test, KIND 0: y adjacent to t (ts: t's alive-adjacency set, h = 2
-// detection); KIND 1: t in B2_new(y) (radius-3 tests).  The lanes' row pieces are laid end
-// to end and the warp walks the concatenation 32 x kWalkUnroll slots per step, each lane
-// finding the piece its slot belongs to by a binary search over the running lengths; the
-// walk skips kept pairs and stops once none is pending.  Returns the lanes kept (the same
-// mask in every lane).  Called by whole warps.
-template <int KIND>
-__device__ __forceinline__ unsigned warp_walk_rows(const LossArgs &a, bool want, int rb, int from, int to,
-                                                   int t, const uint32_t *ts, int round, unsigned &reads) {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int len = (want && to > from) ? to - from : 0;
-    const int incl = warp_incl_scan(len);
-    const int excl = incl - len;
-    const int total = __shfl_sync(full, incl, 31);
-    const int start = rb + from;
-    unsigned pending = __ballot_sync(full, len > 0);
-    unsigned kept = 0u;
-    for (int base = 0; base < total && pending; base += 32 * kWalkUnroll) {
-        int y[kWalkUnroll], own[kWalkUnroll];
-#pragma unroll
-        for (int j = 0; j < kWalkUnroll; j++) {
-            const int idx = base + 32 * j + lane;
-            // owner lane: the number of lanes whose pieces end at or before idx
-            int o = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1)
-                if (__shfl_sync(full, incl, o + step - 1) <= idx) o += step;
-            o = min(o, 31);
-            const int ex = __shfl_sync(full, excl, o), so = __shfl_sync(full, start, o);
-            own[j] = o;
-            y[j] = (idx < total && ((pending >> o) & 1u)) ? a.col_live[so + idx - ex] : -1;
-        }
-        unsigned hits = 0u;
-#pragma unroll
-        for (int j = 0; j < kWalkUnroll; j++) {
-            const int to_ = __shfl_sync(full, t, own[j]);
-            if (KIND == 0) {
-                const uint32_t *tsj = reinterpret_cast<const uint32_t *>(
-                    __shfl_sync(full, reinterpret_cast<unsigned long long>(ts), own[j]));
-                if (y[j] >= 0) {
-                    reads++;
-                    if (alive_adjacent_set(a, tsj, to_, y[j], reads)) hits |= 1u << own[j];
-                }
-            } else if (y[j] >= 0) {
-                reads++;
-                if (in_b2_new(a, y[j], to_, round, reads)) hits |= 1u << own[j];
-            }
-        }
-        hits = __reduce_or_sync(full, hits);
-        kept |= hits;
-        pending &= ~hits;
-    }
-    return kept;
-}
-
-// Slots one chunk of a handed-over walk covers (one step of warp_walk_rows).
-constexpr int kWalkChunk = 32 * kWalkUnroll;
-
-// Slots of a row walked by the warp that found the pair before the rest is handed over.
-constexpr int kDeferMin = 256;
-
-// Hands the rest of the lanes' walks (slots [from, len) of row w at rb) to k_loss_walk:
-// one pair record per lane and one chunk entry per kWalkChunk slots.  A lane whose pair or
-// chunks do not fit the lists keeps its walk (returns false; its reserved chunk entries
-// are written as unused).  The pair is then decided by the walk kernel: lost (recorded as
-// (x, z) at edge side u) iff no chunk finds the test's neighbour.  Called by whole warps.
-__device__ __forceinline__ bool defer_walk(const LossArgs &a, DevStatus *st, bool want, int kind, int w, int t,
-                                           int x, int z, int u, int rb, int from, int len) {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    // lists already full: no reservation (keeps the counters bounded)
-    if (want && (vload(st->ndpairs) >= a.dpairs_cap || vload(st->ndchunks) >= a.dchunks_cap)) want = false;
-    const int nch = want ? (len - from + kWalkChunk - 1) / kWalkChunk : 0;
-    const unsigned wb = __ballot_sync(full, want);
-    if (wb == 0u) return false;
-    const int cincl = warp_incl_scan(nch);
-    const int ctot = __shfl_sync(full, cincl, 31);
-    int pbase = 0, cbase = 0;
-    if (lane == 0) {
-        pbase = atomicAdd(&st->ndpairs, __popc(wb));
-        cbase = atomicAdd(&st->ndchunks, ctot);
-    }
-    pbase = __shfl_sync(full, pbase, 0);
-    cbase = __shfl_sync(full, cbase, 0);
-    const int pi = pbase + __popc(wb & lanemask_lt());
-    const int c0 = cbase + cincl - nch;
-    const bool ok = want && pi < a.dpairs_cap && c0 + nch <= a.dchunks_cap;
-    if (ok) {
-        a.dpairs[2 * pi] = make_int4(w, t, x, z);
-        a.dpairs[2 * pi + 1] = make_int4(u, 2 * nch + kind, rb, len);
-    }
-    unsigned todo = __ballot_sync(full, nch > 0);
-    while (todo) {
-        const int l = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int cl = __shfl_sync(full, c0, l), cn = __shfl_sync(full, nch, l);
-        const int pl = __shfl_sync(full, pi, l), fl = __shfl_sync(full, from, l);
-        const int okl = __shfl_sync(full, ok ? 1 : 0, l);
-        for (int c = lane; c < cn && cl + c < a.dchunks_cap; c += 32)
-            a.dchunks[cl + c] = okl ? make_int2(pl, fl + c * kWalkChunk) : make_int2(-1, 0);
-    }
-    return ok;
-}
-
 // Common alive neighbours for the warp's hard pairs (lanes with state == kHard; p the
-// shorter row, (x, z) the pair as detection names it, u its edge side): the first
-// defer_min slots of each row are walked here; the rows still undecided after that are
-// handed to k_loss_walk (their pairs stay unrecorded here), or walked to the end here when
-// the hand-over lists are full.  Called by whole warps.
-__device__ __forceinline__ void warp_hard_pairs(const LossArgs &a, DevStatus *st, int &state, int p, int q,
-                                                int x, int z, int u, unsigned &reads) {
+// shorter row), all at once: the pairs' rows of p are laid end to end and the warp walks
+// the concatenation 32 x kWalkUnroll slots per step, each lane finding the pair its slot belongs to by a
+// binary search over the lanes' running row lengths.  A pair is kept at its first alive
+// neighbour that q also has; the walk skips kept pairs and stops once none is pending.
+// Called by whole warps.
+__device__ __forceinline__ void warp_hard_pairs(const LossArgs &a, int &state, int p, int q,
+                                                unsigned &reads) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const bool hard = state == kHard;
@@ -374,16 +234,42 @@ __device__ __forceinline__ void warp_hard_pairs(const LossArgs &a, DevStatus *st
         qset = hub_set(a, q, reads);
         reads += 2;
     }
-    const int cap = a.defer_min > 0 ? a.defer_min : INT_MAX;
-    unsigned kept = warp_walk_rows<0>(a, hard, rb, 0, min(len, cap), q, qset, 0, reads);
-    const bool rest = hard && !((kept >> lane) & 1u) && len > cap;
-    bool deferred = false;
-    if (__any_sync(full, rest)) {
-        deferred = defer_walk(a, st, rest, 0, p, q, x, z, u, rb, cap, len);
-        const bool inl = rest && !deferred;
-        if (__any_sync(full, inl)) kept |= warp_walk_rows<0>(a, inl, rb, cap, len, q, qset, 0, reads);
+    const int incl = warp_incl_scan(len);
+    const int excl = incl - len;
+    const int total = __shfl_sync(full, incl, 31);
+    unsigned pending = __ballot_sync(full, hard);
+    unsigned kept = 0u;
+    for (int base = 0; base < total && pending; base += 32 * kWalkUnroll) {
+        int y[kWalkUnroll], own[kWalkUnroll];
+#pragma unroll
+        for (int j = 0; j < kWalkUnroll; j++) {
+            const int idx = base + 32 * j + lane;
+            // owner lane: the number of lanes whose rows end at or before idx
+            int o = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(full, incl, o + step - 1) <= idx) o += step;
+            o = min(o, 31);
+            const int ex = __shfl_sync(full, excl, o), rbo = __shfl_sync(full, rb, o);
+            own[j] = o;
+            y[j] = (idx < total && ((pending >> o) & 1u)) ? a.col_live[rbo + idx - ex] : -1;
+        }
+        unsigned hits = 0u;
+#pragma unroll
+        for (int j = 0; j < kWalkUnroll; j++) {
+            const int qo = __shfl_sync(full, q, own[j]);
+            const uint32_t *qs = reinterpret_cast<const uint32_t *>(
+                __shfl_sync(full, reinterpret_cast<unsigned long long>(qset), own[j]));
+            if (y[j] >= 0) {
+                reads++;
+                if (alive_adjacent_set(a, qs, qo, y[j], reads)) hits |= 1u << own[j];
+            }
+        }
+        hits = __reduce_or_sync(full, hits);
+        kept |= hits;
+        pending &= ~hits;
     }
-    if (hard) state = (((kept >> lane) & 1u) || deferred) ? kKept : kLost;
+    if (hard) state = ((kept >> lane) & 1u) ? kKept : kLost;
 }
 
 // Is w in the stored ball of z (dense words, or sorted (word index, word) pairs)?
@@ -662,7 +548,7 @@ __device__ void ph_detect(const LossArgs &a) {
             pairs++;
             state = pair_quick(a, p, q, reads);
         }
-        if (__any_sync(0xffffffffu, state == kHard)) warp_hard_pairs(a, st, state, p, q, r.x, z, u, reads);
+        if (__any_sync(0xffffffffu, state == kHard)) warp_hard_pairs(a, state, p, q, reads);
         record_lost_warp(a, st, state == kLost, r.x, z, u, reads);
         reads_total += reads;
     }
@@ -828,6 +714,31 @@ __device__ void ph_apply(const LossArgs &a) {
 // their own pair set) has listed first.  Radius-3 losses then take the support deltas of
 // the h = 2 rounds unchanged, on B3.
 
+// Is the pair {p,q} among this round's radius-2 losses?
+__device__ __forceinline__ bool lost2_now(const LossArgs &a, int p, int q, unsigned &bytes) {
+    const unsigned long long key = pair_key(p, q);
+    unsigned long long slot = mix64(key) & a.cap2_mask;
+    for (unsigned long long probe = 0; probe <= a.cap2_mask; probe++) {
+        const unsigned long long k = a.keys2[slot];
+        bytes += 8;
+        if (k == key) return true;
+        if (k == kEmpty) return false;
+        slot = (slot + 1) & a.cap2_mask;
+    }
+    return false;
+}
+
+// q in B2_new(z): the stored radius-2 bit, unless this round lost the pair (the pair set is
+// probed only for vertices that lost a radius-2 member this round).
+__device__ __forceinline__ bool in_b2_new(const LossArgs &a, int z, int q, int round, unsigned &bytes) {
+    bytes += 4;
+    if (!((a.pool2[(int64_t)z * a.Wpad + (q >> 5)] >> (q & 31)) & 1u)) return false;
+    if (z == q) return true;
+    bytes += 4;
+    if (a.touch2[z] != round) return true;
+    return !lost2_now(a, z, q, bytes);
+}
+
 // Position of the k-th (0-based) set bit of v (k < popc(v)).
 __device__ __forceinline__ int nth_set_bit(uint32_t v, int k) {
     for (; k > 0; k--) v &= v - 1u;
@@ -893,11 +804,10 @@ __device__ void ph_c3_items(const LossArgs &a) {
 
 // Common walk of the warp's hard radius-3 pairs (lanes with state == kHard): w is the
 // endpoint whose alive row is walked, t the other one; the pair is kept at the first alive
-// neighbour y of w with t in B2_new(y).  As for detection, rows still undecided after
-// defer_min slots go to k_loss_walk (the pair (p, q) is recorded there if lost).  Called by
-// whole warps.
-__device__ __forceinline__ void warp_walk3(const LossArgs &a, DevStatus *st, int &state, int w, int t,
-                                           int p, int q, int round, unsigned &reads) {
+// neighbour y of w with t in B2_new(y).  The rows are laid end to end and walked 128 slots
+// per step as in warp_hard_pairs.  Called by whole warps.
+__device__ __forceinline__ void warp_walk3(const LossArgs &a, int &state, int w, int t, int round,
+                                           unsigned &reads) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const bool hard = state == kHard;
@@ -907,16 +817,39 @@ __device__ __forceinline__ void warp_walk3(const LossArgs &a, DevStatus *st, int
         len = a.row_ptr[w + 1] - rb;
         reads += 2;
     }
-    const int cap = a.defer_min > 0 ? a.defer_min : INT_MAX;
-    unsigned kept = warp_walk_rows<1>(a, hard, rb, 0, min(len, cap), t, nullptr, round, reads);
-    const bool rest = hard && !((kept >> lane) & 1u) && len > cap;
-    bool deferred = false;
-    if (__any_sync(full, rest)) {
-        deferred = defer_walk(a, st, rest, 1, w, t, p, q, 0, rb, cap, len);
-        const bool inl = rest && !deferred;
-        if (__any_sync(full, inl)) kept |= warp_walk_rows<1>(a, inl, rb, cap, len, t, nullptr, round, reads);
+    const int incl = warp_incl_scan(len);
+    const int excl = incl - len;
+    const int total = __shfl_sync(full, incl, 31);
+    unsigned pending = __ballot_sync(full, hard);
+    unsigned kept = 0u;
+    for (int base = 0; base < total && pending; base += 128) {
+        int y[4], own[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int idx = base + 32 * j + lane;
+            int o = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(full, incl, o + step - 1) <= idx) o += step;
+            o = min(o, 31);
+            const int ex = __shfl_sync(full, excl, o), rbo = __shfl_sync(full, rb, o);
+            own[j] = o;
+            y[j] = (idx < total && ((pending >> o) & 1u)) ? a.col_live[rbo + idx - ex] : -1;
+        }
+        unsigned hits = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int to = __shfl_sync(full, t, own[j]);
+            if (y[j] >= 0) {
+                reads++;
+                if (in_b2_new(a, y[j], to, round, reads)) hits |= 1u << own[j];
+            }
+        }
+        hits = __reduce_or_sync(full, hits);
+        kept |= hits;
+        pending &= ~hits;
     }
-    if (hard) state = (((kept >> lane) & 1u) || deferred) ? kKept : kLost;
+    if (hard) state = ((kept >> lane) & 1u) ? kKept : kLost;
 }
 
 // Tests the lanes' radius-3 candidate pairs {p,q} (q < 0: none; q is in B3_old(p)) in the
@@ -935,7 +868,7 @@ __device__ __forceinline__ void test_pairs3(const LossArgs &a, DevStatus *st, in
             }
         }
     }
-    if (__any_sync(0xffffffffu, state == kHard)) warp_walk3(a, st, state, w, t, p, q, round, reads);
+    if (__any_sync(0xffffffffu, state == kHard)) warp_walk3(a, state, w, t, round, reads);
     record_lost_warp(a, st, state == kLost, p, q, 0, reads);
 }
 
@@ -1014,74 +947,6 @@ __device__ void ph_test3(const LossArgs &a) {
         atomicAdd((unsigned long long *)&st->st_c3_pairs, s_pairs);
         atomicAdd(&st->st_bytes_detect, 4ull * s_reads);
     }
-}
-
-// The handed-over walks, one warp per 128-slot chunk: a chunk whose pair is already kept
-// is skipped, otherwise it looks for the pair's neighbour (test as in warp_walk_rows) and
-// marks the pair kept.  The warp that finishes a pair's last chunk decides it: lost iff no
-// chunk marked it, then recorded as the loss tests would have; it also clears the pair's
-// flags for the next batch.
-__device__ void ph_walk(const LossArgs &a) {
-    __shared__ unsigned long long s_reads;
-    DevStatus *st = a.st;
-    if (threadIdx.x == 0) s_reads = 0ull;
-    __syncthreads();
-    const unsigned full = 0xffffffffu;
-    const int nch = min(vload(st->ndchunks), a.dchunks_cap), round = vload(st->round);
-    const int lane = threadIdx.x & 31;
-    unsigned long long reads_total = 0ull;
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nch; c += nwarps) {
-        const int2 ch = a.dchunks[c];
-        if (ch.x < 0) continue;
-        const int4 P = a.dpairs[2 * ch.x], Q = a.dpairs[2 * ch.x + 1];
-        int *flag = a.dflag + 2 * ch.x;
-        const int kind = Q.y & 1, chunks = Q.y >> 1;
-        unsigned reads = 0;
-        int done = 0;
-        if (lane == 0) done = vload(flag[0]);
-        done = __shfl_sync(full, done, 0);
-        if (!done) {
-            const int end = min(Q.w, ch.y + kWalkChunk);
-            const uint32_t *ts = kind == 0 ? hub_set(a, P.y, reads) : nullptr;
-            int y[kWalkUnroll];
-#pragma unroll
-            for (int j = 0; j < kWalkUnroll; j++) {
-                const int idx = ch.y + 32 * j + lane;
-                y[j] = idx < end ? a.col_live[Q.z + idx] : -1;
-            }
-            bool hit = false;
-#pragma unroll
-            for (int j = 0; j < kWalkUnroll; j++) {
-                if (y[j] < 0) continue;
-                reads++;
-                hit |= kind == 0 ? alive_adjacent_set(a, ts, P.y, y[j], reads)
-                                 : in_b2_new(a, y[j], P.y, round, reads);
-            }
-            if (__any_sync(full, hit) && lane == 0) atomicExch(flag, 1);
-        }
-        int last = 0;
-        if (lane == 0) {
-            __threadfence();
-            last = atomicAdd(flag + 1, 1) == chunks - 1;
-        }
-        last = __shfl_sync(full, last, 0);
-        if (last) {
-            int lost = 0;
-            if (lane == 0) {
-                __threadfence();
-                lost = vload(flag[0]) == 0;
-                flag[0] = 0;
-                flag[1] = 0;
-            }
-            record_lost_warp(a, st, lane == 0 && lost, P.z, P.w, Q.x, reads);
-        }
-        reads_total += reads;
-    }
-    for (int o = 16; o > 0; o >>= 1) reads_total += __shfl_xor_sync(full, reads_total, o);
-    if (lane == 0 && reads_total) atomicAdd(&s_reads, reads_total);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_reads) atomicAdd(&st->st_bytes_detect, 4ull * s_reads);
 }
 
 // Clears the round's radius-2 losses from the stored B2 (and their pair-set slots).
@@ -1220,11 +1085,6 @@ __global__ void __launch_bounds__(kBlock) k_loss3_test(LossArgs a) {
     if (round_idle(a)) return;
     ph_test3(a);
 }
-__global__ void __launch_bounds__(kBlock) k_loss_walk(LossArgs a) {
-    phase_entry();
-    if (round_idle(a)) return;
-    ph_walk(a);
-}
 __global__ void __launch_bounds__(kBlock) k_loss_delta(LossArgs a) {
     phase_entry();
     if (round_idle(a)) return;
@@ -1335,13 +1195,6 @@ LossArgs loss_args(Handle *H) {
     a.c3items_cap = (int32_t)w.c3items_cap;
     a.c3items = w.c3items;
     a.touch2 = w.touch2;
-    // the test table (128 slots) also hands over walks early, into lists of 4 pairs
-    a.defer_min = w.lost_tiny ? 16 : kDeferMin;
-    a.dpairs_cap = (int32_t)w.dpairs_cap;
-    a.dchunks_cap = (int32_t)w.dchunks_cap;
-    a.dpairs = w.dpairs;
-    a.dflag = w.dflag;
-    a.dchunks = w.dchunks;
     return a;
 }
 
@@ -1351,7 +1204,6 @@ LossArgs loss_args(Handle *H) {
 // every block that can be resident at once, as a cooperative launch requires.
 htd_status launch_persistent_rounds(Handle *H, cudaStream_t s, int max_slots, int64_t *launches) {
     LossArgs a = loss_args(H);
-    a.defer_min = 0;  // no walk phase between its grid barriers: every walk stays in its warp
     static thread_local int grid_cached = 0, dev_cached = -1;
     if (grid_cached == 0 || dev_cached != H->g.device) {
         int occ = 0;
@@ -1380,24 +1232,22 @@ namespace {
 // Blocks of one full wave of a phase kernel (every block resident at once), per device.
 struct PhaseGrids {
     int device = -1;
-    int detect = 0, delta = 0, test3 = 0, walk = 0;
+    int detect = 0, delta = 0, test3 = 0;
 };
 
 htd_status phase_grids(Handle *H, PhaseGrids &pg) {
     if (pg.device == H->g.device) return HTD_OK;
-    int od = 0, ou = 0, ot = 0, ow = 0;
+    int od = 0, ou = 0, ot = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, k_loss_detect, kBlock, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_loss_delta, kBlock, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ot, k_loss3_test, kBlock, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ow, k_loss_walk, kBlock, 0) != cudaSuccess ||
-        od < 1 || ou < 1 || ot < 1 || ow < 1) {
+        od < 1 || ou < 1 || ot < 1) {
         set_last_error("incremental round: no resident block fits");
         return HTD_ECUDA;
     }
     pg.detect = H->num_sms * od;
     pg.delta = H->num_sms * ou;
     pg.test3 = H->num_sms * ot;
-    pg.walk = H->num_sms * ow;
     pg.device = H->g.device;
     return HTD_OK;
 }
@@ -1421,7 +1271,7 @@ cudaError_t launch_phase(void (*kernel)(LossArgs), int grid, cudaStream_t s, boo
 
 }  // namespace
 
-// Enqueues one incremental round as five launches, h = 1: four, h = 3: six (the graph path).  evs (nullable):
+// Enqueues one incremental round as four launches (the graph path).  evs (nullable):
 // kRoundEvents events; phases are marked as select | - | detect | update | - | reduce.
 // Without events the launches are programmatic (each overlaps the previous one's tail).
 htd_status enqueue_incremental_round(Handle *H, cudaStream_t s, int64_t *launches, cudaEvent_t *evs,
@@ -1442,36 +1292,32 @@ htd_status enqueue_incremental_round(Handle *H, cudaStream_t s, int64_t *launche
         // select | radius-2 detection + radius-3 items | radius-3 tests | updates | - | reduce
         LossArgs a2 = a;
         a2.rec_r2 = 1;
-        a2.defer_min = 0;  // the radius-2 detection keeps its walks (no walk phase after it)
         mark(0);
         if (e == cudaSuccess) e = launch_phase(k_inc_select, grid_scan, s, pdl, a);
         mark(1);
         if (e == cudaSuccess) e = launch_phase(k_loss_detect, pg.detect, s, pdl, a2);
         mark(2);
         if (e == cudaSuccess) e = launch_phase(k_loss3_test, pg.test3, s, pdl, a);
-        if (e == cudaSuccess) e = launch_phase(k_loss_walk, pg.walk, s, pdl, a);
         mark(3);
         if (e == cudaSuccess) e = launch_phase(k_loss_delta, pg.delta, s, pdl, a);
         mark(4);
         mark(5);
         if (e == cudaSuccess) e = launch_phase(k_loss_apply_reduce, grid_scan, s, pdl, a);
         mark(6);
-        *launches += 6;
+        *launches += 5;
     } else {
         mark(0);
         if (e == cudaSuccess) e = launch_phase(k_inc_select, grid_scan, s, pdl, a);
         mark(1);
         mark(2);
         if (e == cudaSuccess) e = launch_phase(k_loss_detect, pg.detect, s, pdl, a);
-        // h = 1 detection has no walks
-        if (e == cudaSuccess && a.h >= 2) e = launch_phase(k_loss_walk, pg.walk, s, pdl, a);
         mark(3);
         if (e == cudaSuccess) e = launch_phase(k_loss_delta, pg.delta, s, pdl, a);
         mark(4);
         mark(5);
         if (e == cudaSuccess) e = launch_phase(k_loss_apply_reduce, grid_scan, s, pdl, a);
         mark(6);
-        *launches += a.h >= 2 ? 5 : 4;
+        *launches += 4;
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {

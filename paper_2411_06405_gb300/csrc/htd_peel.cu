@@ -635,9 +635,6 @@ void free_work(PeelWork *w) {
     cudaFree(w->lost2);
     cudaFree(w->c3items);
     cudaFree(w->touch2);
-    cudaFree(w->dpairs);
-    cudaFree(w->dflag);
-    cudaFree(w->dchunks);
     cudaFree(w->status);
     if (w->status_host) cudaFreeHost(w->status_host);
     *w = PeelWork{};
@@ -750,14 +747,6 @@ htd_status ensure_work_impl(Handle *H, int32_t h, bool incremental, bool tiny_ta
         w.uitems_cap = 2 * w.lost_max + w.upd_budget / 32 + 1024;
         HTD_CHECK(alloc_n(&w.pitems, w.pitems_cap));
         HTD_CHECK(alloc_n(&w.uitems, w.uitems_cap));
-        // long walks of the loss tests (with the tiny table too few, so that most of them
-        // stay in the warp that found them)
-        w.dpairs_cap = tiny_table ? 4 : ((int64_t)1 << 16);
-        w.dchunks_cap = tiny_table ? 64 : ((int64_t)1 << 20);
-        HTD_CHECK(alloc_n(&w.dpairs, 2 * w.dpairs_cap));
-        HTD_CHECK(alloc_n(&w.dflag, 2 * w.dpairs_cap));
-        HTD_CHECK(cudaMemsetAsync(w.dflag, 0, 2 * w.dpairs_cap * sizeof(int32_t), H->pstream));
-        HTD_CHECK(alloc_n(&w.dchunks, w.dchunks_cap));
         if (h == 3) {
             // radius-2 balls (dense) with their own metadata, the round's radius-2 losses and
             // the radius-3 candidate items
@@ -1012,8 +1001,6 @@ __global__ void k_recover_reset(DevStatus *st) {
     st->npitems = 0;
     st->nuitems = 0;
     st->nc3items = 0;
-    st->ndpairs = 0;
-    st->ndchunks = 0;
     st->upd_work = 0;
     st->overflow_unit = INT_MAX;
     for (int j = 0; j < kMaxH; j++) st->cand_cnt[j] = 0;

@@ -74,8 +74,6 @@ __device__ __forceinline__ void round_finalize(DevStatus *st, int initial) {
     st->nlost = 0;
     st->nlost2 = 0;
     st->nc3items = 0;
-    st->ndpairs = 0;
-    st->ndchunks = 0;
     st->npitems = 0;
     st->nuitems = 0;
     st->upd_work = 0;

@@ -244,8 +244,6 @@ int64_t htd_footprint_estimate(int32_t n, int64_t m_in, int32_t h, int64_t free_
     // CSR and per-edge peel state (each edge: 2 slots x (col, slot id, live mark) and 8 per-edge
     // int32 arrays), per-vertex arrays, work items and the staging buffers of the request
     double bytes = 4.0 * (6.0 * M + 8.0 * M) + 4.0 * 24.0 * N + 8.0 * (N + 2.0 * M / 64.0) + 5.0 * 4.0 * M;
-    // the lists of long walks the incremental rounds hand to their chunk kernel
-    if (h <= 3) bytes += 12.0 * (1 << 20);
     // balls: dense n-bit sets per vertex when they fit (radius h, plus radius 2 at h = 3,
     // plus the alive-adjacency sets), else about 16 words per vertex in the compact form
     const double W = (double)(((int64_t)n + 31) / 32 + 3) / 4.0 * 4.0;
