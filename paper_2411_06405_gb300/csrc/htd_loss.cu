@@ -745,8 +745,11 @@ __device__ __forceinline__ int nth_set_bit(uint32_t v, int k) {
     return __ffs(v) - 1;
 }
 
-// Words of a B2 row one radius-3 candidate item scans.
-constexpr int kC3Words = 32;
+// Words of a B2 row one radius-3 candidate item scans: at most 128 candidates, so that one
+// item never holds up its launch (one GB300, DC-SBM n = 200,000 at h = 3: 3.7 s per
+// decomposition with 4 words, 4.2 s with 16, 5.1 s with 32; 2 words made more rounds
+// overflow the item list).
+constexpr int kC3Words = 4;
 
 // Radius-3 candidate items of the round's frontier, one warp per frontier edge (a,b):
 //   (a, row b, word range) and (b, row a, word range): {a} x B2_old(b) and {b} x B2_old(a);
