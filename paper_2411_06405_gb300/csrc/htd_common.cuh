@@ -62,7 +62,7 @@ struct DevStatus {
     // incremental h = 3 rounds (radius-2 balls kept beside the radius-3 support balls)
     int32_t nlost2;            // radius-2 lost-pair records of the current round
     int32_t halt;              // 1: a round ran out of room; the host finishes it by rebuilds
-    long long nc3items;        // radius-3 candidate items of the current round (64-bit: the
+    long long nc3items;        // stored radius-3 candidate items of the current round (64-bit: the
                                // reservations of a huge round may pass 2^31 before it halts)
     int64_t st_c3_pairs;       // radius-3 candidate pairs tested
     int64_t st_lost2;          // radius-2 lost pairs

@@ -157,10 +157,6 @@ __device__ __forceinline__ bool alive_adjacent_set(const LossArgs &a, const uint
     return false;
 }
 
-__device__ __forceinline__ bool alive_adjacent(const LossArgs &a, int p, int q, unsigned &reads) {
-    return alive_adjacent_set(a, hub_set(a, p, reads), p, q, reads);
-}
-
 // Short rows are scanned by one lane; pairs whose shorter row is longer go to the warp.
 constexpr int kInlineScan = 8;
 
@@ -751,32 +747,38 @@ __device__ __forceinline__ int nth_set_bit(uint32_t v, int k) {
 // overflow the item list).
 constexpr int kC3Words = 4;
 
-// Radius-3 candidate items of the round's frontier, one warp per frontier edge (a,b):
-//   (a, row b, word range) and (b, row a, word range): {a} x B2_old(b) and {b} x B2_old(a);
-//   (p, row b, 32 slots) for every old neighbour p != b of a: N_old(a) x N_old(b).
-// Item layout: (x, y, first word | first slot, -1 - end word | end slot).
+// Radius-3 candidate items of the round's frontier.  For each frontier edge F[f] = (a,b):
+//   (a, row b, word range) and (b, row a, word range): {a} x B2_old(b) and {b} x B2_old(a),
+//     2 * nch items per edge, not stored: item index i < 2 * nch * |F| is frontier edge
+//     i / (2 nch), side (i % (2 nch)) / nch, word chunk i % nch (c3_range_item);
+//   (p, row b, 32 slots) for every old neighbour p != b of a: N_old(a) x N_old(b), written
+//     by one warp per frontier edge into the item list.
+// Item layout: (x, y, first word | first slot, -1 - end word | end slot).  A round whose
+// items (both kinds) exceed the list's capacity halts.
+__device__ __forceinline__ int c3_chunks(const LossArgs &a) { return (a.Wpad + kC3Words - 1) / kC3Words; }
+
+__device__ __forceinline__ int4 c3_range_item(const LossArgs &a, int i, int nch) {
+    const int f = i / (2 * nch), r = i - f * 2 * nch;
+    const int side = r >= nch, ch = side ? r - nch : r;
+    const int e = a.frontier[f];
+    const int ea = a.eu[e], eb = a.ev[e];
+    const int w0 = ch * kC3Words, w1 = min(a.Wpad, w0 + kC3Words);
+    return side ? make_int4(eb, ea, w0, -1 - w1) : make_int4(ea, eb, w0, -1 - w1);
+}
+
 __device__ void ph_c3_items(const LossArgs &a) {
     DevStatus *st = a.st;
     const int nF = vload(st->nF), round = vload(st->round);
     const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    const int nch = (a.Wpad + kC3Words - 1) / kC3Words;
+    const long long nA = 2ll * c3_chunks(a) * nF;
+    if (nA > a.c3items_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&st->halt, 1);
+        return;
+    }
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nF; i += nwarps) {
         const int e = a.frontier[i];
         const int ea = a.eu[e], eb = a.ev[e];
-        long long base = 0;
-        if (lane == 0) base = (long long)atomicAdd((unsigned long long *)&st->nc3items,
-                                                   (unsigned long long)(2 * nch));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base + 2 * nch > a.c3items_cap) {
-            if (lane == 0) atomicOr(&st->halt, 1);
-        } else {
-            for (int c = lane; c < 2 * nch; c += 32) {
-                const int side = c / nch, ch = c % nch;
-                const int w0 = ch * kC3Words, w1 = min(a.Wpad, w0 + kC3Words);
-                a.c3items[base + c] = side ? make_int4(eb, ea, w0, -1 - w1) : make_int4(ea, eb, w0, -1 - w1);
-            }
-        }
         const int rba = a.row_ptr[ea], rea = a.row_ptr[ea + 1];
         const int rbb = a.row_ptr[eb], reb = a.row_ptr[eb + 1];
         const int nb = (reb - rbb + 31) >> 5;
@@ -794,7 +796,7 @@ __device__ void ph_c3_items(const LossArgs &a) {
             if (lane == 31 && tot)
                 b2 = (long long)atomicAdd((unsigned long long *)&st->nc3items, (unsigned long long)tot);
             b2 = __shfl_sync(0xffffffffu, b2, 31);
-            if (b2 + tot > a.c3items_cap) {
+            if (nA + b2 + tot > a.c3items_cap) {
                 if (lane == 0 && tot) atomicOr(&st->halt, 1);
                 continue;
             }
@@ -884,13 +886,19 @@ __device__ void ph_test3(const LossArgs &a) {
         s_reads = 0ull;
     }
     __syncthreads();
-    const int nitems = (int)min(vload(st->nc3items), (long long)a.c3items_cap);
+    // a round whose items passed the capacity has halted (this kernel is then idle), so
+    // both counts fit the list here
+    const int nch = c3_chunks(a);
+    const long long nA64 = 2ll * nch * vload(st->nF);
+    if (nA64 > a.c3items_cap) return;
+    const int nA = (int)nA64;
+    const int nitems = nA + (int)min(vload(st->nc3items), (long long)a.c3items_cap - nA);
     const int round = vload(st->round);
     const int lane = threadIdx.x & 31;
     unsigned long long pairs = 0ull, reads_total = 0ull;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nwarps) {
-        const int4 item = a.c3items[it];
+        const int4 item = it < nA ? c3_range_item(a, it, nch) : a.c3items[it - nA];
         const int x = item.x, y = item.y;
         unsigned reads = 0;
         if (item.w < 0) {
