@@ -746,6 +746,9 @@ __device__ __forceinline__ int nth_set_bit(uint32_t v, int k) {
 // decomposition with 4 words, 4.2 s with 16, 5.1 s with 32; 2 words made more rounds
 // overflow the item list).
 constexpr int kC3Words = 4;
+// Range items one warp tests per step (kC3Words lanes each).
+constexpr int kC3Groups = 32 / kC3Words;
+static_assert(32 % kC3Words == 0, "range items must tile a warp");
 
 // Radius-3 candidate items of the round's frontier.  For each frontier edge F[f] = (a,b):
 //   (a, row b, word range) and (b, row a, word range): {a} x B2_old(b) and {b} x B2_old(a),
@@ -897,52 +900,62 @@ __device__ void ph_test3(const LossArgs &a) {
     const int lane = threadIdx.x & 31;
     unsigned long long pairs = 0ull, reads_total = 0ull;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nwarps) {
-        const int4 item = it < nA ? c3_range_item(a, it, nch) : a.c3items[it - nA];
-        const int x = item.x, y = item.y;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // {x} x B2_old(y) restricted to B3_old(x), kC3Groups range items per warp and step: the
+    // lanes of group g hold the words of item (step * kC3Groups + g) * nwarps + warp (items
+    // of one warp step lie far apart, so their candidate counts average out), and the
+    // step's candidates are dealt out 32 at a time by a warp prefix sum
+    for (int s0 = 0; s0 * kC3Groups * nwarps < nA; s0++) {
+        const int it = (s0 * kC3Groups + lane / kC3Words) * nwarps + gw;
+        int x = -1, wi = 0;
+        uint32_t bits = 0u;
         unsigned reads = 0;
-        if (item.w < 0) {
-            // {x} x B2_old(y), restricted to B3_old(x): lane i holds word item.z + i of the
-            // AND; the warp's candidates are dealt out 32 at a time in order
-            const int w1 = -1 - item.w;
-            const int wi = item.z + lane;
-            uint32_t bits = 0u;
-            if (wi < w1) {
-                bits = a.pool2[(int64_t)y * a.Wpad + wi] & a.pool[(int64_t)x * a.Wpad + wi];
+        if (it < nA) {
+            const int4 item = c3_range_item(a, it, nch);
+            x = item.x;
+            wi = item.z + lane % kC3Words;
+            if (wi < -1 - item.w) {
+                bits = a.pool2[(int64_t)item.y * a.Wpad + wi] & a.pool[(int64_t)x * a.Wpad + wi];
                 reads += 2;
                 if (wi == (x >> 5)) bits &= ~(1u << (x & 31));
             }
-            const int cnt = __popc(bits);
-            const int incl = warp_incl_scan(cnt);
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            for (int t0 = 0; t0 < total; t0 += 32) {
-                const int idx = t0 + lane;
-                // owner lane: the number of lanes whose candidates end at or before idx
-                int o = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (__shfl_sync(0xffffffffu, incl, o + step - 1) <= idx) o += step;
-                o = min(o, 31);
-                const uint32_t ob = __shfl_sync(0xffffffffu, bits, o);
-                const int ex = __shfl_sync(0xffffffffu, incl - cnt, o);
-                int q = -1;
-                if (idx < total) q = ((item.z + o) << 5) + nth_set_bit(ob, idx - ex);
-                test_pairs3(a, st, x, q, round, reads, pairs);
-            }
-        } else {
-            // {x} x N_old(y) for the slots of the item, restricted to B3_old(x)
-            const int sl = item.z + lane;
-            int q = -1;
-            if (sl < item.w) {
-                const int c = a.col[sl], cl = a.col_live[sl];
-                reads += 2;
-                if (c != x && (cl >= 0 || cl == -(round + 1))) {
-                    reads++;
-                    if ((a.pool[(int64_t)x * a.Wpad + (c >> 5)] >> (c & 31)) & 1u) q = c;
-                }
-            }
-            test_pairs3(a, st, x, q, round, reads, pairs);
         }
+        const int cnt = __popc(bits);
+        const int incl = warp_incl_scan(cnt);
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int idx = t0 + lane;
+            // owner lane: the number of lanes whose candidates end at or before idx
+            int o = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(0xffffffffu, incl, o + step - 1) <= idx) o += step;
+            o = min(o, 31);
+            const uint32_t ob = __shfl_sync(0xffffffffu, bits, o);
+            const int ex = __shfl_sync(0xffffffffu, incl - cnt, o);
+            const int ow = __shfl_sync(0xffffffffu, wi, o), ox = __shfl_sync(0xffffffffu, x, o);
+            int q = -1;
+            if (idx < total) q = (ow << 5) + nth_set_bit(ob, idx - ex);
+            test_pairs3(a, st, ox, q, round, reads, pairs);
+        }
+        reads_total += reads;
+    }
+    // {x} x N_old(y) for the 32 slots of a stored item, restricted to B3_old(x): one per warp
+    for (int it = nA + gw; it < nitems; it += nwarps) {
+        const int4 item = a.c3items[it - nA];
+        const int x = item.x;
+        unsigned reads = 0;
+        const int sl = item.z + lane;
+        int q = -1;
+        if (sl < item.w) {
+            const int c = a.col[sl], cl = a.col_live[sl];
+            reads += 2;
+            if (c != x && (cl >= 0 || cl == -(round + 1))) {
+                reads++;
+                if ((a.pool[(int64_t)x * a.Wpad + (c >> 5)] >> (c & 31)) & 1u) q = c;
+            }
+        }
+        test_pairs3(a, st, x, q, round, reads, pairs);
         reads_total += reads;
     }
     for (int o = 16; o > 0; o >>= 1) {
