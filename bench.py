@@ -237,7 +237,7 @@ def _phase_classes(st, h):
     timed = max(1, st["timed_slots"])
     if st["incremental"] and h == 3:
         return [("k_inc_select", st["ms_select"] / timed),
-                ("k_loss_detect (radius 2, radius-3 items)", st["ms_remove"] / timed),
+                ("k_loss_detect3 (radius-2 detection, radius-3 items)", st["ms_remove"] / timed),
                 ("k_loss3_test", st["ms_find"] / timed),
                 ("k_loss_delta", st["ms_update"] / timed),
                 ("k_loss_apply_reduce", st["ms_minreduce"] / timed)]
@@ -336,7 +336,7 @@ def measure_workload(htd, torch, lib, name, h, steps, warmup, flush, stream, dev
     hb = round_bytes_host(spec.n, host_np(eu), host_np(evv), host_np(stamp), h)
     if stp["incremental"] and h == 3:
         phases["k_inc_select"]["alg_bytes_host"] = hb["select"]
-        phases["k_loss_detect (radius 2, radius-3 items)"]["alg_bytes_host"] = hb["detect"]
+        phases["k_loss_detect3 (radius-2 detection, radius-3 items)"]["alg_bytes_host"] = hb["detect"]
         phases["k_loss3_test"]["alg_bytes_kernel"] = stp["alg_bytes_detect"]
         phases["k_loss_delta"]["alg_bytes_kernel"] = stp["alg_bytes_update"]
     elif stp["incremental"]:

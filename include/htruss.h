@@ -157,7 +157,7 @@ htd_status htd_edges(const htd_graph *g, int32_t *eu_dev, int32_t *ev_dev, void 
 htd_status htd_csr(const htd_graph *g, int32_t *row_ptr_dev, int32_t *col_dev,
                    int32_t *slot_eid_dev, void *stream);
 
-/* h-support of every edge (Def. 2, Def. 3; the parallel loop of Algorithm 2, lines 1-3):
+/* h-support of every edge (Def. 2, Def. 3; the initial h-support loop of Algorithm 2):
  * sup_dev[e] = |N(u,h) ∩ N(v,h)| in the whole graph, u and v excluded.
  * sup_dev: device buffer of m int32.  1 <= h <= HTD_MAX_H. */
 htd_status htd_h_support(htd_graph *g, int32_t h, int32_t *sup_dev, void *stream);

@@ -11,7 +11,7 @@
  *   (validity)     sup_T(e,h) >= t(e) - 2 in T = {e' : t(e') >= t(e)}          (Def. 4);
  *   (removability) sup_G(e,h) <= t(e) - 2 in G = {e' : stamp(e') >= stamp(e)},  i.e. e
  *                  qualified for removal at level t(e) in the graph left when it was
- *                  removed (Sec. 3, Algorithm 1, lines 7-10).
+ *                  removed (Sec. 3, Algorithm 1, its removal step).
  * Validity makes every T_k = {t >= k} satisfy Def. 4, so t(e) is at most the true
  * trussness.  If some e had a larger true trussness K, the edge e* of the (K,h)-truss with
  * the smallest stamp would have h-support >= K - 2 in its removal graph; removability gives

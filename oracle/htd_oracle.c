@@ -172,8 +172,8 @@ int32_t htdo_edge_h_support(htdo_graph *g, int32_t h, const int32_t *key, int32_
 }
 
 /* h-support of every edge of the subgraph {key[e] >= thr} (all edges when key is NULL);
- * sup_out[e] = -1 for edges outside it.  This is the parallel loop of Algorithm 2
- * (lines 1-3) and lines 2-4 of Algorithm 1, run one edge after the other. */
+ * sup_out[e] = -1 for edges outside it.  This is the initial h-support loop of
+ * Algorithm 2 and of Algorithm 1, run one edge after the other. */
 void htdo_h_support(htdo_graph *g, int32_t h, const int32_t *key, int32_t thr,
                     int32_t *sup_out) {
     for (int64_t e = 0; e < g->m; e++) {
@@ -221,7 +221,7 @@ int64_t htdo_truss_decompose(htdo_graph *g, int32_t h, int32_t *t_out, int32_t *
 /* Algorithm 1 taken literally, one edge at a time: bins indexed by sup+2, k from 2 to
  * ubtruss = max sup + 2; pick the smallest-id edge of bin[k], assign t = k, delete it,
  * then for every remaining edge whose h-support is above k-2 recompute its h-support and
- * move it to bin[max(sup+2, k)].  The affected set of line 11 is taken as every remaining
+ * move it to bin[max(sup+2, k)].  The affected set E_G(e,h) of Algorithm 1 is taken as every remaining
  * edge (a superset of any reading of it).  Returns 0, or -1 on allocation failure. */
 int32_t htdo_truss_sequential(htdo_graph *g, int32_t h, int32_t *t_out) {
     int64_t m = g->m;
@@ -261,7 +261,7 @@ int32_t htdo_truss_sequential(htdo_graph *g, int32_t h, int32_t *t_out) {
  *   (validity)    sup_{T}(e,h) >= t(e)-2 in T = {e' : t(e') >= t(e)}  (Def. 4 (i));
  *   (removability) sup_{G_s}(e,h) <= t(e)-2 in G_s = {e' : stamp(e') >= stamp(e)},
  *                  i.e. e qualified for removal at level t(e) in the graph left when it
- *                  was removed (Algorithm 1, lines 7-10).
+ *                  was removed (Algorithm 1, its removal step).
  * Together with stamps ordered like t (htdo_check_stamp_order) these imply t is the exact
  * h-trussness.  fail_out[i] gets 0 (ok), 1 (validity fails) or 2 (removability fails).
  * Returns the number of failing edges. */

@@ -320,7 +320,7 @@ htd_status hindex_run(htd_graph *G, Handle *H, int32_t h, int32_t sweeps, int32_
     cudaFree(lists);
     lists = nullptr;
     {
-        // H^(0) = sup(e,h), the h-support of every edge (Algorithm 2, lines 1-3)
+        // H^(0) = sup(e,h), the h-support of every edge (the initial step of Algorithm 2)
         HX_CHECK(cudaMalloc(&key, m * 4));
         HX_CHECK(cudaMalloc(&key2, m * 4));
         htd_status hs = htd_h_support(G, h, key, s);

@@ -996,7 +996,7 @@ __device__ void ph_apply2(const LossArgs &a) {
 }
 
 // One candidate edge per lane (p: it joins the frontier): warp-aggregated frontier slot,
-// removal (Algorithm 1, lines 8-10) and the detection items of its two edge sides.  Whole
+// removal (the removal step of Algorithm 1) and the detection items of its two edge sides.  Whole
 // warps call it.
 __device__ __forceinline__ void select_one(const LossArgs &a, DevStatus *st, bool p, int e, int k,
                                            int round) {
@@ -1057,7 +1057,7 @@ __device__ __forceinline__ void select_one(const LossArgs &a, DevStatus *st, boo
 }
 
 // Phase 1 of an incremental round: every alive edge with h-support <= k-2 joins F and is
-// removed at once (Algorithm 1, lines 7-10), and the loss detection items of its two edge
+// removed at once (the selection and removal steps of Algorithm 1), and the loss detection items of its two edge
 // sides are written.  A continued round only writes the items of its remaining sides.
 __device__ void ph_select_items(const LossArgs &a) {
     DevStatus *st = a.st;
@@ -1097,12 +1097,17 @@ __global__ void __launch_bounds__(kBlock) k_inc_select(LossArgs a) {
     if (round_idle(a)) return;
     ph_select_items(a);
 }
-// h = 3: the radius-2 detection (a.rec_r2) and the round's radius-3 candidate items
 __global__ void __launch_bounds__(kBlock) k_loss_detect(LossArgs a) {
     phase_entry();
     if (round_idle(a)) return;
     ph_detect(a);
-    if (a.h3) ph_c3_items(a);
+}
+// h = 3: the radius-2 detection (a.rec_r2) and the round's radius-3 candidate items
+__global__ void __launch_bounds__(kBlock) k_loss_detect3(LossArgs a) {
+    phase_entry();
+    if (round_idle(a)) return;
+    ph_detect(a);
+    ph_c3_items(a);
 }
 __global__ void __launch_bounds__(kBlock) k_loss3_test(LossArgs a) {
     phase_entry();
@@ -1256,20 +1261,22 @@ namespace {
 // Blocks of one full wave of a phase kernel (every block resident at once), per device.
 struct PhaseGrids {
     int device = -1;
-    int detect = 0, delta = 0, test3 = 0;
+    int detect = 0, detect3 = 0, delta = 0, test3 = 0;
 };
 
 htd_status phase_grids(Handle *H, PhaseGrids &pg) {
     if (pg.device == H->g.device) return HTD_OK;
-    int od = 0, ou = 0, ot = 0;
+    int od = 0, od3 = 0, ou = 0, ot = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, k_loss_detect, kBlock, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od3, k_loss_detect3, kBlock, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_loss_delta, kBlock, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ot, k_loss3_test, kBlock, 0) != cudaSuccess ||
-        od < 1 || ou < 1 || ot < 1) {
+        od < 1 || od3 < 1 || ou < 1 || ot < 1) {
         set_last_error("incremental round: no resident block fits");
         return HTD_ECUDA;
     }
     pg.detect = H->num_sms * od;
+    pg.detect3 = H->num_sms * od3;
     pg.delta = H->num_sms * ou;
     pg.test3 = H->num_sms * ot;
     pg.device = H->g.device;
@@ -1319,7 +1326,7 @@ htd_status enqueue_incremental_round(Handle *H, cudaStream_t s, int64_t *launche
         mark(0);
         if (e == cudaSuccess) e = launch_phase(k_inc_select, grid_scan, s, pdl, a);
         mark(1);
-        if (e == cudaSuccess) e = launch_phase(k_loss_detect, pg.detect, s, pdl, a2);
+        if (e == cudaSuccess) e = launch_phase(k_loss_detect3, pg.detect3, s, pdl, a2);
         mark(2);
         if (e == cudaSuccess) e = launch_phase(k_loss3_test, pg.test3, s, pdl, a);
         mark(3);

@@ -12,7 +12,7 @@ namespace htd {
 // and the kernel returns.
 constexpr unsigned kBarrierSpinLimit = 1u << 24;
 
-// Removes edge e at level k in round `round` (Algorithm 1, lines 8-10): t(e) = k, its
+// Removes edge e at level k in round `round` (the removal step of Algorithm 1): t(e) = k, its
 // stamp, a support no selection matches, both adjacency slots marked dead with the round
 // (-(round + 1), so a slot tells by itself whether it died in the current round), alive
 // degrees and (when present) the endpoints' alive-adjacency sets updated.
