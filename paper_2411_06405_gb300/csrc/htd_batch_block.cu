@@ -64,16 +64,6 @@ __device__ __forceinline__ int bb_block_min(int v, int *s_red) {
     return r;
 }
 
-__device__ __forceinline__ int bb_block_sum(int v, int *s_red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    int r = 0;
-    for (int j = 0; j < kBBWarps; j++) r += s_red[j];
-    __syncthreads();
-    return r;
-}
-
 __global__ void __launch_bounds__(kBB) k_batch_block(const BlockGraphDesc *__restrict__ gd, int32_t count,
                                                      BlockScratch sc, int32_t *queue,
                                                      unsigned long long *rounds_total,
