@@ -80,6 +80,8 @@ def _load():
         lib.htdo_check_stamp_order.restype = i64
         lib.htdo_hindex.argtypes = [p, i32, i32, i32, p, p]
         lib.htdo_hindex.restype = i32
+        lib.htdo_hindex_pruned.argtypes = [p, i32, i32, p, p, p]
+        lib.htdo_hindex_pruned.restype = i32
         lib.htdo_certify_all.argtypes = [i32, i64, p, p, i32, p, p, i32, p, p, p, p]
         lib.htdo_certify_all.restype = i64
         _lib = lib
@@ -168,6 +170,18 @@ class OracleGraph:
         if rc < 0:
             raise MemoryError("oracle H-index iteration: allocation failed")
         return hv[: self.m], int(it.value), rc == 1
+
+    def hindex_pruned(self, h: int, max_iter: int = -1):
+        """Synchronous H-index iteration with the Lemma 4 pruning of Sec. 4.  Returns (H
+        values, orders computed, converged, H^(n)(e) evaluations actually computed)."""
+        hv = np.zeros(max(1, self.m), dtype=np.int32)
+        it = ctypes.c_int32()
+        ev = ctypes.c_int64()
+        rc = self._lib.htdo_hindex_pruned(self._g, int(h), int(max_iter), _ptr(hv),
+                                          ctypes.byref(it), ctypes.byref(ev))
+        if rc < 0:
+            raise MemoryError("oracle pruned H-index iteration: allocation failed")
+        return hv[: self.m], int(it.value), rc == 1, int(ev.value)
 
     def certify(self, h: int, t, stamp, edges=None):
         """Peeling certificate: returns (stamp_order_violations, failing_edges, fail_codes).

@@ -438,3 +438,71 @@ done:
     free(cur); free(nxt); free(pu); free(pv); free(tmp); free(vals);
     return rc;
 }
+
+/* Synchronous H-index iteration with the redundant-computation pruning of Sec. 4 (Lemma 4):
+ * from order 2 on, H^(n)(e) is not computed but set to H^(n-1)(e) when no edge e' of
+ * E_G(e,h) fell across T = H^(n-1)(e) in the previous order, i.e. when every e' has
+ * H^(n-2)(e') = H^(n-1)(e') (case i), H^(n-2)(e') < T (case ii) or H^(n-1)(e') >= T
+ * (case iii).  Reading of E_G(e,h), which the paper leaves undefined here: every edge with
+ * an endpoint within distance h-1 of u or of v in G, which holds every edge of a path of
+ * at most h edges from u or from v (the paths the keys of H^(n)(e) come from).  Outputs as
+ * htdo_hindex; evals_out (nullable) receives the number of H^(n)(e) actually computed.
+ * Returns 1 if converged, 0 if stopped at max_iter, -1 on allocation failure. */
+int32_t htdo_hindex_pruned(htdo_graph *g, int32_t h, int32_t max_iter, int32_t *hv_out,
+                           int32_t *iters_out, int64_t *evals_out) {
+    int64_t m = g->m;
+    size_t mm = (size_t)(m > 0 ? m : 1), nn = (size_t)(g->n > 0 ? g->n : 1);
+    int32_t *old = (int32_t *)malloc(mm * sizeof(int32_t));   /* H^(n-2) */
+    int32_t *cur = (int32_t *)malloc(mm * sizeof(int32_t));   /* H^(n-1) */
+    int32_t *nxt = (int32_t *)malloc(mm * sizeof(int32_t));   /* H^(n)   */
+    int32_t *pu = (int32_t *)malloc(nn * sizeof(int32_t));
+    int32_t *pv = (int32_t *)malloc(nn * sizeof(int32_t));
+    int32_t *tmp = (int32_t *)malloc(nn * sizeof(int32_t));
+    int32_t *vals = (int32_t *)malloc(nn * sizeof(int32_t));
+    int32_t rc = 0, n = 0;
+    int64_t evals = 0;
+    if (!old || !cur || !nxt || !pu || !pv || !tmp || !vals) { rc = -1; goto done; }
+    htdo_h_support(g, h, NULL, 0, cur);
+    int64_t cap = 1;
+    for (int64_t e = 0; e < m; e++) cap += cur[e];
+    for (;;) {
+        if (max_iter >= 0 && n >= max_iter) break;
+        if (n >= cap) break;
+        int changed = 0;
+        for (int64_t e = 0; e < m; e++) {
+            int needed = 1;
+            if (n >= 1) {
+                /* was any edge of E_G(e,h) across T = H^(n-1)(e) in the previous order? */
+                int32_t T = cur[e], u = g->eu[e], v = g->ev[e];
+                int64_t na = ball_bfs(g, u, h - 1, NULL, 0, g->dist_a, g->queue_a);
+                int64_t nb = ball_bfs(g, v, h - 1, NULL, 0, g->dist_b, g->queue_b);
+                needed = 0;
+                for (int64_t f = 0; f < m && !needed; f++) {
+                    int32_t a = g->eu[f], b = g->ev[f];
+                    int in = g->dist_a[a] >= 0 || g->dist_a[b] >= 0 || g->dist_b[a] >= 0 ||
+                             g->dist_b[b] >= 0;
+                    if (in && old[f] >= T && cur[f] < T) needed = 1;
+                }
+                ball_reset(g->dist_a, g->queue_a, na);
+                ball_reset(g->dist_b, g->queue_b, nb);
+            }
+            if (needed) {
+                nxt[e] = hindex_edge(g, h, cur, e, pu, pv, tmp, vals);
+                if (nxt[e] < 0) { rc = -1; goto done; }
+                evals++;
+            } else {
+                nxt[e] = cur[e];
+            }
+            if (nxt[e] != cur[e]) changed = 1;
+        }
+        int32_t *t = old; old = cur; cur = nxt; nxt = t;
+        n++;
+        if (!changed) { rc = 1; break; }
+    }
+    if (m > 0) memcpy(hv_out, cur, (size_t)m * sizeof(int32_t));
+done:
+    if (iters_out) *iters_out = n;
+    if (evals_out) *evals_out = evals;
+    free(old); free(cur); free(nxt); free(pu); free(pv); free(tmp); free(vals);
+    return rc;
+}

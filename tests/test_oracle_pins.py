@@ -330,3 +330,50 @@ def test_hindex_h1_is_the_triangle_hindex(oracle_mod):
         for k in range(7):
             hv, _, _ = g.hindex(1, max_iter=k)
             np.testing.assert_array_equal(hv, ref[k], err_msg=f"order {k}")
+
+
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_hindex_pruning_changes_no_order(oracle_mod, h):
+    # Lemma 4: an edge whose neighbourhood had no value fall across its own H in the
+    # previous order keeps its H.  The pruned iteration must equal the plain synchronous
+    # one order by order (same values after every order, same number of orders) while
+    # computing fewer H^(n)(e); the fixed point + 2 is still t(e,h)
+    skipped = 0
+    for seed in range(5):
+        s, d = erdos_renyi_gnm(28, 90, 7500 + 10 * h + seed)
+        g = oracle_mod.OracleGraph.from_raw(28, s, d)
+        _, final, _ = g.hindex(h)
+        for k in range(final + 1):
+            ref, it_ref, conv_ref = g.hindex(h, max_iter=k)
+            hv, it, conv, evals = g.hindex_pruned(h, max_iter=k)
+            np.testing.assert_array_equal(hv, ref, err_msg=f"h={h} seed={seed} order {k}")
+            assert (it, conv) == (it_ref, conv_ref)
+            assert evals <= g.m * it
+        hv, it, conv, evals = g.hindex_pruned(h)
+        assert conv and it == final
+        np.testing.assert_array_equal(hv + 2, g.truss_decompose(h)[0])
+        skipped += g.m * it - evals
+    assert skipped > 0
+
+
+def test_hindex_pruning_is_not_vacuous(oracle_mod):
+    # a planted mistake in the rule (pruning whenever the edge's own value did not change
+    # in the previous order, ignoring its neighbourhood) must give a different result on
+    # some graph, so the test above can tell a wrong rule from the right one
+    differs = False
+    for seed in range(12):
+        s, d = erdos_renyi_gnm(24, 80, 7700 + seed)
+        g = oracle_mod.OracleGraph.from_raw(24, s, d)
+        ref, final, _ = g.hindex(2)
+        prev = g.hindex(2, max_iter=0)[0]
+        cur = g.hindex(2, max_iter=1)[0]
+        wrong = cur.copy()
+        for k in range(2, final + 1):
+            nxt_full = g.hindex(2, max_iter=k)[0]
+            nxt = np.where(cur == prev, cur, nxt_full)  # the planted rule
+            prev, cur = cur, nxt
+            wrong = nxt
+        if not np.array_equal(wrong, ref):
+            differs = True
+            break
+    assert differs
