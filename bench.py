@@ -482,18 +482,21 @@ def measure_batched(htd, torch, count: int, seed: int, steps: int, warmup: int, 
 
 def measure_hindex(htd, torch, name: str, h: int, sweeps_list=(1, 8)):
     """The paper's H-index iteration (Sec. 4) on a workload: orders to the fixed point and
-    device time, synchronous (Algorithm 2) and with asynchronous updating by edge blocks;
-    the fixed point + 2 is checked against the peel of the same graph."""
+    device time, synchronous (Algorithm 2), with asynchronous updating by edge blocks, and
+    synchronous with the Lemma 4 pruning (H^(n)(e) computed, summed over the orders); the
+    fixed point + 2 is checked against the peel of the same graph."""
     spec = config_graph(name)
     g = htd.htd_build_csr(spec.n, torch.from_numpy(spec.src).cuda(), torch.from_numpy(spec.dst).cuda())
     t_peel, _, _ = htd.htd_truss_decompose(g, h)
     out = {"workload": f"{name}_h{h}_hindex", "m": g.m}
-    for sw in sweeps_list:
-        t, _, st = htd.htd_hindex_decompose(g, h, sweeps=sw)
-        out[f"sweeps_{sw}"] = {"orders": st["iterations"], "converged": st["converged"],
-                               "ms": st["ms_total"], "edges_per_sec": g.m / (st["ms_total"] / 1e3),
-                               "ball_entries": st["ball_entries"],
-                               "equals_peel": bool(torch.equal(t, t_peel))}
+    runs = [(f"sweeps_{sw}", sw, False) for sw in sweeps_list] + [("sweeps_1_pruned", 1, True)]
+    for label, sw, prune in runs:
+        t, _, st = htd.htd_hindex_decompose(g, h, sweeps=sw, prune=prune)
+        out[label] = {"orders": st["iterations"], "converged": st["converged"],
+                      "ms": st["ms_total"], "edges_per_sec": g.m / (st["ms_total"] / 1e3),
+                      "ball_entries": st["ball_entries"], "edge_evals": st["edge_evals"],
+                      "vertex_evals": st["vertex_evals"],
+                      "equals_peel": bool(torch.equal(t, t_peel))}
     g.free()
     return out
 

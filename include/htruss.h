@@ -282,7 +282,9 @@ typedef struct htd_hindex_stats {
     int32_t iterations;      /* orders computed (the last one changed nothing if converged) */
     int32_t converged;
     float ms_total;          /* device time of the call (CUDA events) */
-    int32_t pad;
+    int32_t pruned;          /* 1 if the orders used the Lemma 4 pruning */
+    int64_t edge_evals;      /* H^(n)(e) computed, summed over the orders */
+    int64_t vertex_evals;    /* vertices whose path keys were computed, summed over the orders */
 } htd_hindex_stats;
 
 /* Runs the H-index iteration from H^(0) = sup(e,h) until an order changes nothing (or for
@@ -296,6 +298,18 @@ typedef struct htd_hindex_stats {
 htd_status htd_hindex_decompose(htd_graph *g, int32_t h, int32_t sweeps, int32_t max_iter,
                                 int32_t *truss_dev, int32_t *hval_dev, htd_hindex_stats *stats,
                                 void *stream);
+
+/* Options of htd_hindex_decompose_ex. */
+#define HTD_HX_PRUNE 1u  /* redundant-computation pruning (Sec. 4, Lemma 4), synchronous orders
+                            only: from the second order on, an edge keeps H^(n-1) without being
+                            computed when no edge within h-1 hops of its endpoints fell across
+                            its value in the previous order.  Same values after every order. */
+
+/* htd_hindex_decompose with option flags (HTD_HX_*).  EINVAL also for unknown flags and for
+ * HTD_HX_PRUNE with sweeps != 1. */
+htd_status htd_hindex_decompose_ex(htd_graph *g, int32_t h, int32_t sweeps, int32_t max_iter,
+                                   uint32_t flags, int32_t *truss_dev, int32_t *hval_dev,
+                                   htd_hindex_stats *stats, void *stream);
 
 /* ---- Served decomposition: a request loop with continuous batching -------------------
  *

@@ -252,17 +252,21 @@ def htd_h_support_static(n: int, row_ptr, col, eu, ev, h: int, out, stream=None)
     return out
 
 
-def htd_hindex_decompose(g: Graph, h: int, sweeps: int = 1, max_iter: int = -1, stream=None):
+def htd_hindex_decompose(g: Graph, h: int, sweeps: int = 1, max_iter: int = -1, stream=None,
+                         prune: bool = False):
     """The H-index iteration of Sec. 4 on the device.  sweeps = 1: synchronous orders
-    (Algorithm 2); sweeps > 1: asynchronous updating by that many edge blocks per order.
-    Returns (truss = H + 2, H, stats dict) as int32 CUDA tensors of m entries."""
+    (Algorithm 2); sweeps > 1: asynchronous updating by that many edge blocks per order;
+    prune (sweeps = 1 only): the redundant-computation pruning of Lemma 4
+    (htd_hindex_decompose_ex with HTD_HX_PRUNE).  Returns (truss = H + 2, H, stats dict) as
+    int32 CUDA tensors of m entries."""
     torch = _torch()
     t = torch.empty(max(g.m, 1), dtype=torch.int32, device=g.device)
     hv = torch.empty(max(g.m, 1), dtype=torch.int32, device=g.device)
     st = _lib.HtdHindexStats()
-    _lib.check(_lib.load().htd_hindex_decompose(g.handle, int(h), int(sweeps), int(max_iter),
-                                                _ptr(t), _ptr(hv), ctypes.byref(st),
-                                                _stream_handle(stream)), "htd_hindex_decompose")
+    _lib.check(_lib.load().htd_hindex_decompose_ex(g.handle, int(h), int(sweeps), int(max_iter),
+                                                   _lib.HTD_HX_PRUNE if prune else 0,
+                                                   _ptr(t), _ptr(hv), ctypes.byref(st),
+                                                   _stream_handle(stream)), "htd_hindex_decompose")
     return t[:g.m], hv[:g.m], st.as_dict()
 
 

@@ -26,6 +26,7 @@ HTD_OPT_TINY_LOSS_TABLE = 8
 HTD_OPT_PERSISTENT_ROUNDS = 16
 HTD_OPT_COMPACT_BALLS = 32
 HTD_OPT_BATCH_BLOCKS = 64
+HTD_HX_PRUNE = 1
 
 # every symbol include/htruss.h declares
 EXPORTED = (
@@ -33,7 +34,7 @@ EXPORTED = (
     "htd_truss_decompose", "htd_truss_decompose_ex", "htd_truss_decompose_host",
     "htd_graph_free", "htd_kernel_launch_count", "htd_status_string", "htd_last_error",
     "htd_h_support_static", "htd_truss_decompose_batched", "htd_batch_plan",
-    "htd_hindex_decompose", "htd_footprint_estimate", "htd_server_create", "htd_server_submit", "htd_server_poll",
+    "htd_hindex_decompose", "htd_hindex_decompose_ex", "htd_footprint_estimate", "htd_server_create", "htd_server_submit", "htd_server_poll",
     "htd_server_wait", "htd_server_info", "htd_server_destroy",
 )
 
@@ -90,11 +91,13 @@ class HtdHindexStats(ctypes.Structure):
         ("iterations", ctypes.c_int32),
         ("converged", ctypes.c_int32),
         ("ms_total", ctypes.c_float),
-        ("pad", ctypes.c_int32),
+        ("pruned", ctypes.c_int32),
+        ("edge_evals", ctypes.c_int64),
+        ("vertex_evals", ctypes.c_int64),
     ]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class HtdRequestInfo(ctypes.Structure):
@@ -175,6 +178,8 @@ def load():
             "htd_batch_plan": ([i32, p, p, p, i32, p, p, ctypes.POINTER(i32)], ctypes.c_int),
             "htd_hindex_decompose": ([p, i32, i32, i32, p, p, ctypes.POINTER(HtdHindexStats), p],
                                      ctypes.c_int),
+            "htd_hindex_decompose_ex": ([p, i32, i32, i32, u32, p, p, ctypes.POINTER(HtdHindexStats), p],
+                                        ctypes.c_int),
             "htd_footprint_estimate": ([i32, i64, i32, i64], i64),
             "htd_server_create": ([i32, i64, u32, pp], ctypes.c_int),
             "htd_server_submit": ([p, i32, p, p, i64, i32, ctypes.POINTER(i64)], ctypes.c_int),

@@ -546,18 +546,27 @@ htd_status htd_truss_decompose_ex(htd_graph *g, int32_t h, uint32_t flags, int32
     return HTD_OK;
 }
 
-htd_status htd_hindex_decompose(htd_graph *g, int32_t h, int32_t sweeps, int32_t max_iter,
-                                int32_t *truss_dev, int32_t *hval_dev, htd_hindex_stats *stats,
-                                void *stream) {
-    if (!g || h < 1 || h > HTD_MAX_H || sweeps < 1 || sweeps > 4096) {
-        set_last_error("htd_hindex_decompose: NULL handle, h outside [1, HTD_MAX_H] or sweeps outside [1, 4096]");
+htd_status htd_hindex_decompose_ex(htd_graph *g, int32_t h, int32_t sweeps, int32_t max_iter,
+                                   uint32_t flags, int32_t *truss_dev, int32_t *hval_dev,
+                                   htd_hindex_stats *stats, void *stream) {
+    if (!g || h < 1 || h > HTD_MAX_H || sweeps < 1 || sweeps > 4096 || (flags & ~HTD_HX_PRUNE) != 0u ||
+        ((flags & HTD_HX_PRUNE) && sweeps != 1)) {
+        set_last_error("htd_hindex_decompose: NULL handle, h outside [1, HTD_MAX_H], sweeps outside "
+                       "[1, 4096], unknown flags, or pruning with sweeps != 1");
         return HTD_EINVAL;
     }
     Handle *H = &g->H;
     cudaStream_t user = static_cast<cudaStream_t>(stream);
     API_TRY(begin_call(H, user));
-    API_TRY(htd::hindex_run(g, H, h, sweeps, max_iter, truss_dev, hval_dev, stats, H->pstream));
+    API_TRY(htd::hindex_run(g, H, h, sweeps, max_iter, (flags & HTD_HX_PRUNE) != 0u, truss_dev, hval_dev,
+                            stats, H->pstream));
     return end_call(H, user);
+}
+
+htd_status htd_hindex_decompose(htd_graph *g, int32_t h, int32_t sweeps, int32_t max_iter,
+                                int32_t *truss_dev, int32_t *hval_dev, htd_hindex_stats *stats,
+                                void *stream) {
+    return htd_hindex_decompose_ex(g, h, sweeps, max_iter, 0u, truss_dev, hval_dev, stats, stream);
 }
 
 htd_status htd_truss_decompose(htd_graph *g, int32_t h, int32_t *truss_dev, int32_t *stamp_dev,

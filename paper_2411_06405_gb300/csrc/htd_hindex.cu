@@ -20,7 +20,13 @@
 //                  excluded), their values min(P(u,w), P(v,w)) gathered in a per-warp
 //                  buffer, and H(.) by a binary search on y of the monotone test
 //                  "at least y values >= y".
-// Synchronous orders (Algorithm 2) write the new keys to a second array.  The asynchronous
+// Synchronous orders (Algorithm 2) write the new keys to a second array.  With pruning
+// (Lemma 4), from the second order on an edge keeps its key without being computed when no
+// edge near it fell across that key in the previous order: per vertex, the range of the
+// fallen edges' values (lowest new, highest old) is spread h-1 hops, and an edge whose two
+// endpoints' ranges do not straddle its key is skipped (the range hull is a conservative
+// form of the lemma's per-edge conditions, so the result is unchanged); path keys are then
+// computed only at the endpoints of the edges still listed.  The asynchronous
 // form splits every sweep into S sub-sweeps over consecutive edge-id ranges: a sub-sweep
 // recomputes the path keys of the vertices its edges touch from the current keys and
 // writes its edges' keys in place, so later sub-sweeps already use them (the paper's
@@ -172,8 +178,10 @@ __global__ void __launch_bounds__(kBlock) k_hx_pathkeys(const int32_t *__restric
     }
 }
 
-// New keys of the edges [e0, e1), one warp per edge.  vals: the warp's buffer of maxd.
-__global__ void __launch_bounds__(kBlock) k_hx_edges(int64_t e0, int64_t e1, const int32_t *__restrict__ eu,
+// New keys of the edges [e0, e1) (of elist[e0..e1) when elist is not null), one warp per
+// edge.  vals: the warp's buffer of maxd.
+__global__ void __launch_bounds__(kBlock) k_hx_edges(int64_t e0, int64_t e1, const int32_t *__restrict__ elist,
+                                                    const int32_t *__restrict__ eu,
                                                     const int32_t *__restrict__ ev,
                                                     const int64_t *__restrict__ off,
                                                     const int32_t *__restrict__ members,
@@ -186,7 +194,8 @@ __global__ void __launch_bounds__(kBlock) k_hx_edges(int64_t e0, int64_t e1, con
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int32_t *vals = vals_all + gw * maxd;
     unsigned long long nchg = 0;
-    for (int64_t e = e0 + gw; e < e1; e += nwarps) {
+    for (int64_t i = e0 + gw; i < e1; i += nwarps) {
+        const int64_t e = elist ? elist[i] : i;
         int u = eu[e], v = ev[e];
         int64_t ou = off[u], ov = off[v];
         int lu = (int)(off[u + 1] - ou), lv = (int)(off[v + 1] - ov);
@@ -242,6 +251,71 @@ __global__ void k_hx_touch(int64_t e0, int64_t e1, const int32_t *__restrict__ e
     }
 }
 
+// Pruning, step 1: per vertex, the range of the values that fell at its edges in the
+// previous order: hi = largest H^(n-2), lo = smallest H^(n-1) over its edges that changed.
+__global__ void k_hx_fall(int64_t m, const int32_t *__restrict__ eu, const int32_t *__restrict__ ev,
+                          const int32_t *__restrict__ kold, const int32_t *__restrict__ kcur,
+                          int32_t *hi, int32_t *lo) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = kold[e], b = kcur[e];
+        if (a == b) continue;
+        atomicMax(&hi[eu[e]], a);
+        atomicMin(&lo[eu[e]], b);
+        atomicMax(&hi[ev[e]], a);
+        atomicMin(&lo[ev[e]], b);
+    }
+}
+
+// Pruning, step 2 (h-1 times): one hop of spreading, warp per vertex: the range of x
+// becomes the hull of the ranges of x and its neighbours.
+__global__ void __launch_bounds__(kBlock) k_hx_spread(int32_t n, const int32_t *__restrict__ row_ptr,
+                                                     const int32_t *__restrict__ col,
+                                                     const int32_t *__restrict__ hi_in,
+                                                     const int32_t *__restrict__ lo_in,
+                                                     int32_t *__restrict__ hi_out, int32_t *__restrict__ lo_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = gw; x < n; x += nwarps) {
+        int h = lane == 0 ? hi_in[x] : -1, l = lane == 0 ? lo_in[x] : INT_MAX;
+        for (int s = row_ptr[x] + lane; s < row_ptr[x + 1]; s += 32) {
+            const int y = col[s];
+            h = max(h, hi_in[y]);
+            l = min(l, lo_in[y]);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
+            l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
+        }
+        if (lane == 0) {
+            hi_out[x] = h;
+            lo_out[x] = l;
+        }
+    }
+}
+
+// Pruning, step 3: an edge e = (u,v) with T = H^(n-1)(e) is listed for computation when
+// the hull [min(lo(u), lo(v)), max(hi(u), hi(v))] of the fallen values near it straddles
+// T (some value went from >= T to < T); otherwise H^(n)(e) = T (Lemma 4).  The endpoints of
+// listed edges are listed once each (mark holds the stamp of the order that listed them).
+__global__ void k_hx_select(int64_t m, const int32_t *__restrict__ eu, const int32_t *__restrict__ ev,
+                            const int32_t *__restrict__ kcur, const int32_t *__restrict__ hi,
+                            const int32_t *__restrict__ lo, int32_t *knew, int32_t *elist,
+                            int32_t *ecount, int32_t stamp, int32_t *mark, int32_t *vlist,
+                            int32_t *vcount) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int u = eu[e], v = ev[e], T = kcur[e];
+        const int l = min(lo[u], lo[v]), hh = max(hi[u], hi[v]);
+        if (l < T && T <= hh) {
+            elist[atomicAdd(ecount, 1)] = (int32_t)e;
+            if (atomicExch(&mark[u], stamp) != stamp) vlist[atomicAdd(vcount, 1)] = u;
+            if (atomicExch(&mark[v], stamp) != stamp) vlist[atomicAdd(vcount, 1)] = v;
+        } else {
+            knew[e] = T;
+        }
+    }
+}
+
 // t(e,h) = H(e) + 2 at the fixed point (Theorem 4).
 __global__ void k_hx_truss(int64_t m, const int32_t *__restrict__ hv, int32_t *__restrict__ t) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
@@ -261,14 +335,15 @@ __global__ void k_hx_truss(int64_t m, const int32_t *__restrict__ hv, int32_t *_
 
 }  // namespace
 
-htd_status hindex_run(htd_graph *G, Handle *H, int32_t h, int32_t sweeps, int32_t max_iter,
+htd_status hindex_run(htd_graph *G, Handle *H, int32_t h, int32_t sweeps, int32_t max_iter, bool prune,
                       int32_t *truss_dev, int32_t *hval_dev, htd_hindex_stats *stats, cudaStream_t s) {
     GraphDev &g = H->g;
     const int64_t n = g.n, m = g.m;
     htd_status st = HTD_OK;
     int32_t *sizes = nullptr, *members = nullptr, *P = nullptr, *prev = nullptr, *vals = nullptr;
     int32_t *key = nullptr, *key2 = nullptr, *lists = nullptr, *mark = nullptr, *vlist = nullptr;
-    int32_t *dcount = nullptr;
+    int32_t *dcount = nullptr, *kold = nullptr, *hi = nullptr, *lo = nullptr, *hi2 = nullptr, *lo2 = nullptr;
+    int32_t *elist = nullptr, *decount = nullptr, *hecount = nullptr;
     int64_t *off = nullptr;
     void *tmp = nullptr;
     unsigned long long *dchanged = nullptr, *hchanged = nullptr;
@@ -278,6 +353,7 @@ htd_status hindex_run(htd_graph *G, Handle *H, int32_t h, int32_t sweeps, int32_
     std::memset(&loc, 0, sizeof(loc));
     loc.h = h;
     loc.sweeps = sweeps;
+    loc.pruned = prune ? 1 : 0;
     int64_t launches = 0;
     const int W = (int)std::max<int64_t>(1, (n + 31) / 32);
     const size_t smem = (size_t)W * 4;
@@ -341,6 +417,16 @@ htd_status hindex_run(htd_graph *G, Handle *H, int32_t h, int32_t sweeps, int32_
         HX_CHECK(cudaMalloc(&dcount, 4));
         HX_CHECK(cudaMallocHost(&hcount, 4));
         HX_CHECK(cudaMemsetAsync(mark, 0xff, n * 4, s));
+        if (prune) {
+            HX_CHECK(cudaMalloc(&kold, m * 4));
+            HX_CHECK(cudaMalloc(&hi, n * 4));
+            HX_CHECK(cudaMalloc(&lo, n * 4));
+            HX_CHECK(cudaMalloc(&hi2, n * 4));
+            HX_CHECK(cudaMalloc(&lo2, n * 4));
+            HX_CHECK(cudaMalloc(&elist, m * 4));
+            HX_CHECK(cudaMalloc(&decount, 4));
+            HX_CHECK(cudaMallocHost(&hecount, 4));
+        }
         // every order before the fixed point lowers at least one key (Theorem 3): the sum
         // of H^(0) plus one orders always suffice
         std::vector<int32_t> k0(m);
@@ -354,12 +440,47 @@ htd_status hindex_run(htd_graph *G, Handle *H, int32_t h, int32_t sweeps, int32_
         bool converged = false;
         while (!converged && (max_iter < 0 || it < max_iter) && it < cap) {
             HX_CHECK(cudaMemsetAsync(dchanged, 0, 8, s));
-            if (S == 1) {
+            if (S == 1 && prune && it > 0) {
+                // Lemma 4: list the edges that can still fall (key = H^(n-1), kold = H^(n-2))
+                HX_CHECK(cudaMemsetAsync(hi, 0xff, n * 4, s));
+                HX_CHECK(cudaMemsetAsync(lo, 0x7f, n * 4, s));
+                HX_CHECK(cudaMemsetAsync(dcount, 0, 4, s));
+                HX_CHECK(cudaMemsetAsync(decount, 0, 4, s));
+                k_hx_fall<<<H->num_sms * 4, kBlock, 0, s>>>(m, g.eu, g.ev, kold, key, hi, lo);
+                launches++;
+                for (int r = 1; r < h; r++) {
+                    k_hx_spread<<<H->num_sms * 8, kBlock, 0, s>>>((int32_t)n, g.row_ptr, g.col, hi, lo, hi2, lo2);
+                    launches++;
+                    std::swap(hi, hi2);
+                    std::swap(lo, lo2);
+                }
+                k_hx_select<<<H->num_sms * 4, kBlock, 0, s>>>(m, g.eu, g.ev, key, hi, lo, key2, elist, decount,
+                                                             stamp++, mark, vlist, dcount);
+                launches++;
+                HX_CHECK(cudaMemcpyAsync(hcount, dcount, 4, cudaMemcpyDeviceToHost, s));
+                HX_CHECK(cudaMemcpyAsync(hecount, decount, 4, cudaMemcpyDeviceToHost, s));
+                HX_CHECK(cudaStreamSynchronize(s));
+                if (*hecount > 0) {
+                    k_hx_pathkeys<<<grid_p, kBlock, 0, s>>>(vlist, *hcount, h, g.row_ptr, g.col, g.slot_eid, key,
+                                                            off, members, P, prev, maxb);
+                    k_hx_edges<<<grid_e, kBlock, 0, s>>>(0, *hecount, elist, g.eu, g.ev, off, members, P, key,
+                                                         key2, vals, maxd, dchanged);
+                    launches += 2;
+                }
+                loc.edge_evals += *hecount;
+                loc.vertex_evals += *hcount;
+                // H^(n-2) <- H^(n-1) <- H^(n)
+                std::swap(kold, key);
+                std::swap(key, key2);
+            } else if (S == 1) {
                 k_hx_pathkeys<<<grid_p, kBlock, 0, s>>>(nullptr, (int32_t)n, h, g.row_ptr, g.col, g.slot_eid,
                                                         key, off, members, P, prev, maxb);
-                k_hx_edges<<<grid_e, kBlock, 0, s>>>(0, m, g.eu, g.ev, off, members, P, key, key2, vals, maxd,
-                                                     dchanged);
+                k_hx_edges<<<grid_e, kBlock, 0, s>>>(0, m, nullptr, g.eu, g.ev, off, members, P, key, key2, vals,
+                                                     maxd, dchanged);
                 launches += 2;
+                loc.edge_evals += m;
+                loc.vertex_evals += n;
+                if (prune) std::swap(kold, key);  // with pruning: H^(n-2) <- H^(n-1) <- H^(n)
                 std::swap(key, key2);
             } else {
                 for (int j = 0; j < S; j++) {
@@ -371,9 +492,11 @@ htd_status hindex_run(htd_graph *G, Handle *H, int32_t h, int32_t sweeps, int32_
                     HX_CHECK(cudaStreamSynchronize(s));
                     k_hx_pathkeys<<<grid_p, kBlock, 0, s>>>(vlist, *hcount, h, g.row_ptr, g.col, g.slot_eid, key,
                                                             off, members, P, prev, maxb);
-                    k_hx_edges<<<grid_e, kBlock, 0, s>>>(e0, e1, g.eu, g.ev, off, members, P, key, key, vals,
-                                                         maxd, dchanged);
+                    k_hx_edges<<<grid_e, kBlock, 0, s>>>(e0, e1, nullptr, g.eu, g.ev, off, members, P, key, key,
+                                                         vals, maxd, dchanged);
                     launches += 3;
+                    loc.edge_evals += e1 - e0;
+                    loc.vertex_evals += *hcount;
                 }
             }
             HX_CHECK(cudaGetLastError());
@@ -417,6 +540,14 @@ done:
     cudaFree(mark);
     cudaFree(vlist);
     cudaFree(dcount);
+    cudaFree(kold);
+    cudaFree(hi);
+    cudaFree(lo);
+    cudaFree(hi2);
+    cudaFree(lo2);
+    cudaFree(elist);
+    cudaFree(decount);
+    if (hecount) cudaFreeHost(hecount);
     if (hchanged) cudaFreeHost(hchanged);
     if (hcount) cudaFreeHost(hcount);
     if (t0) cudaEventDestroy(t0);

@@ -162,7 +162,7 @@ htd_status batch_block_run(const std::vector<BlockGraphDescHost> &graphs, cudaSt
                            int num_sms, int64_t *rounds_out);
 
 // The H-index iteration of Sec. 4 on the device (htd_hindex.cu); G is H's public handle.
-htd_status hindex_run(htd_graph *G, Handle *H, int32_t h, int32_t sweeps, int32_t max_iter,
+htd_status hindex_run(htd_graph *G, Handle *H, int32_t h, int32_t sweeps, int32_t max_iter, bool prune,
                       int32_t *truss_dev, int32_t *hval_dev, htd_hindex_stats *stats, cudaStream_t s);
 
 // One incremental round (h <= 3) as four (h = 3: five) launches, the graph path (htd_loss.cu).

@@ -79,6 +79,15 @@ def test_footprint_estimate_on_host(lib):
     assert lib.htd_footprint_estimate(-1, 0, 2, 0) == -1
 
 
+def test_hindex_rejects_bad_arguments_without_a_device(lib):
+    # NULL handle, unknown flags, pruning with asynchronous sweeps: EINVAL before any
+    # device work
+    assert lib.htd_hindex_decompose_ex(None, 2, 1, -1, 0, None, None, None, None) == 1
+    assert lib.htd_hindex_decompose_ex(None, 2, 1, -1, 2, None, None, None, None) == 1
+    assert lib.htd_hindex_decompose_ex(None, 2, 4, -1, 1, None, None, None, None) == 1
+    assert lib.htd_hindex_decompose(None, 2, 1, -1, None, None, None, None) == 1
+
+
 def test_server_rejects_bad_arguments_without_a_device(lib):
     out = ctypes.c_void_p()
     assert lib.htd_server_create(0, 0, 0, ctypes.byref(out)) == 1

@@ -89,6 +89,38 @@ def test_small_workload_and_peel_agree(htd, oracle_mod):
         assert torch.equal(t, t_peel)
 
 
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_pruned_orders_equal_the_plain_orders(htd, oracle_mod, h):
+    # Lemma 4 pruning changes no value of any order: after every order the pruned GPU
+    # iteration equals the plain one (and the oracle's); the GPU's range test is a
+    # conservative form of the oracle's per-edge test, so it computes at least as many
+    # H^(n)(e) as the oracle's pruned iteration and at most m per order
+    graphs = [(n, s, d) for n, s, d in small_corpus(8, 470 + h, max_n=40)]
+    graphs += [(60, *erdos_renyi_gnm(60, 220, 480 + h)), (128, *rmat(7, 6, 0.57, 0.19, 0.19, 490 + h))]
+    saved = 0
+    for n, s, d in graphs:
+        g = gpu_graph(htd, n, s, d)
+        if g.m == 0:
+            continue
+        og = oracle_mod.OracleGraph.from_raw(n, s, d)
+        tp, hp, sp = htd.htd_hindex_decompose(g, h, prune=True)
+        t0, h0, s0 = htd.htd_hindex_decompose(g, h)
+        assert sp["pruned"] == 1 and s0["pruned"] == 0
+        assert sp["converged"] == 1 and sp["iterations"] == s0["iterations"]
+        assert torch.equal(hp, h0) and torch.equal(tp, t0)
+        np.testing.assert_array_equal(tp.cpu().numpy(), og.truss_decompose(h)[0])
+        assert s0["edge_evals"] == g.m * s0["iterations"]
+        assert sp["edge_evals"] <= s0["edge_evals"]
+        _, o_it, _, o_evals = og.hindex_pruned(h)
+        assert o_it == sp["iterations"] and sp["edge_evals"] >= o_evals
+        for k in range(1, min(sp["iterations"], 4) + 1):
+            _, hk, _ = htd.htd_hindex_decompose(g, h, max_iter=k, prune=True)
+            ok, _, _ = og.hindex(h, max_iter=k)
+            np.testing.assert_array_equal(hk.cpu().numpy(), ok, err_msg=f"order {k}")
+        saved += s0["edge_evals"] - sp["edge_evals"]
+    assert saved > 0
+
+
 @pytest.mark.slow
 def test_full_size_dcsbm_h2_equals_the_certified_peel(htd):
     # the GPU peel of this workload is certified on every edge by test_full_size_certificate
@@ -98,6 +130,9 @@ def test_full_size_dcsbm_h2_equals_the_certified_peel(htd):
     t, _, st = htd.htd_hindex_decompose(g, 2, sweeps=1)
     assert st["converged"] == 1
     assert torch.equal(t, t_peel)
+    tp, _, sp = htd.htd_hindex_decompose(g, 2, sweeps=1, prune=True)
+    assert sp["iterations"] == st["iterations"] and torch.equal(tp, t_peel)
+    assert sp["edge_evals"] < st["edge_evals"]
 
 
 def test_bad_arguments(htd):
@@ -105,3 +140,5 @@ def test_bad_arguments(htd):
     for h, sw in ((0, 1), (9, 1), (2, 0)):
         with pytest.raises(htd.HtdError):
             htd.htd_hindex_decompose(g, h, sweeps=sw)
+    with pytest.raises(htd.HtdError):  # pruning is defined for synchronous orders only
+        htd.htd_hindex_decompose(g, 2, sweeps=4, prune=True)
