@@ -377,3 +377,62 @@ def test_hindex_pruning_is_not_vacuous(oracle_mod):
             differs = True
             break
     assert differs
+
+
+def _hull_rule_skips(n, eu, ev, h, old, cur, hops=None):
+    """The GPU's form of the Lemma 4 test, restated on the host: per vertex the range of the
+    values that fell at its edges (highest old, lowest new), widened h-1 hops over the
+    graph; an edge is skipped when its endpoints' hull does not straddle its value."""
+    hi = np.full(n, -1, dtype=np.int64)
+    lo = np.full(n, np.iinfo(np.int64).max, dtype=np.int64)
+    fell = old != cur
+    for x in (eu[fell], ev[fell]):
+        np.maximum.at(hi, x, old[fell])
+        np.minimum.at(lo, x, cur[fell])
+    for _ in range(h - 1 if hops is None else hops):
+        hi2, lo2 = hi.copy(), lo.copy()
+        for a, b in ((eu, ev), (ev, eu)):
+            np.maximum.at(hi2, a, hi[b])
+            np.minimum.at(lo2, a, lo[b])
+        hi, lo = hi2, lo2
+    l = np.minimum(lo[eu], lo[ev])
+    hh = np.maximum(hi[eu], hi[ev])
+    return ~((l < cur) & (cur <= hh))
+
+
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_hindex_range_hull_rule_never_skips_a_change(oracle_mod, h):
+    # the rule the GPU engine uses must only skip edges whose value the next order keeps
+    # (it may compute more than the lemma needs, never less); it must also skip something
+    # (sparser graphs at h = 3, where two hops reach most of a dense small graph)
+    n, m = (30, 100) if h < 3 else (90, 140)
+    skipped = 0
+    for seed in range(6):
+        s, d = erdos_renyi_gnm(n, m, 7900 + 10 * h + seed)
+        g = oracle_mod.OracleGraph.from_raw(n, s, d)
+        _, final, _ = g.hindex(h)
+        orders = [g.hindex(h, max_iter=k)[0].astype(np.int64) for k in range(final + 1)]
+        for k in range(1, final):
+            skip = _hull_rule_skips(n, g.eu, g.ev, h, orders[k - 1], orders[k])
+            np.testing.assert_array_equal(orders[k + 1][skip], orders[k][skip],
+                                          err_msg=f"h={h} seed={seed} order {k + 1}")
+            skipped += int(skip.sum())
+    assert skipped > 0
+
+
+def test_hindex_range_hull_rule_with_one_hop_too_few_fails(oracle_mod):
+    # planted mistake: widening the ranges h-2 hops instead of h-1 at h = 2 (only the
+    # edges at the endpoints themselves) skips an edge that still changes on some graph
+    wrong = False
+    for seed in range(20):
+        s, d = erdos_renyi_gnm(30, 100, 8100 + seed)
+        g = oracle_mod.OracleGraph.from_raw(30, s, d)
+        _, final, _ = g.hindex(2)
+        orders = [g.hindex(2, max_iter=k)[0].astype(np.int64) for k in range(final + 1)]
+        for k in range(1, final):
+            skip = _hull_rule_skips(30, g.eu, g.ev, 2, orders[k - 1], orders[k], hops=0)
+            if not np.array_equal(orders[k + 1][skip], orders[k][skip]):
+                wrong = True
+        if wrong:
+            break
+    assert wrong
