@@ -77,3 +77,24 @@ def test_autotune_group_keys():
     assert autotune.group_key(1000, s, d, 3).startswith("h3_n9_")
     # loops do not count towards degrees; an edgeless graph has class 0
     assert autotune.group_key(5, np.array([1, 1]), np.array([1, 1]), 2) == "h2_n2_d0"
+
+
+def test_autotune_partition_sends_block_groups_to_one_call():
+    # graphs whose group chose one block per graph form the block call; every other graph
+    # (chosen union settings, or a group missing from the table) goes to one union call with
+    # the default settings; every graph lands in exactly one call, in input order
+    from paper_2411_06405_gb300 import _lib, autotune
+
+    s = np.array([0, 1, 2], np.int32)
+    d = np.array([1, 2, 0], np.int32)
+    graphs = [(3, s, d, 2), (3, s, d, 3), (3, s, d, 2), (40, s, d, 2)]
+    table = {autotune.group_key(3, s, d, 2): {"max_union_vertices": 1 << 18,
+                                              "flags": _lib.HTD_OPT_BATCH_BLOCKS},
+             autotune.group_key(3, s, d, 3): {"max_union_vertices": 1 << 16,
+                                              "flags": _lib.HTD_OPT_REBUILD}}
+    parts = autotune._partition(graphs, table)
+    assert parts == [([0, 2], 1 << 18, _lib.HTD_OPT_BATCH_BLOCKS),
+                     ([1, 3], autotune.DEFAULT["max_union_vertices"], autotune.DEFAULT["flags"])]
+    assert autotune._partition(graphs, None) == [([0, 1, 2, 3], autotune.DEFAULT["max_union_vertices"],
+                                                  autotune.DEFAULT["flags"])]
+    assert autotune._partition([], table) == []
